@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Time-to-solution benchmark of the GB300 pipelined BiCGStab library.
+
+Workload: 3-D convection-diffusion, 7-point first-order upwind stencil on a
+256^3 grid (16,777,216 unknowns), velocity (20 sin y, 20 cos z, 20 sin x),
+Dirichlet boundary, FP64; x* ~ U[-1, 1] (SplitMix64, seed 0), b = A x*,
+x0 = 0. One step = one complete pipelined BiCGStab solve (Algorithm 9 with
+residual replacement every 50 iterations) to ||r||/||r0|| <= 1e-8, stencil
+form, inputs resident in HBM. The same line reports standard BiCGStab
+(Algorithm 7) and the CSR form of the same matrix for comparison, the
+end-to-end time through the host-buffer C entry point, the roofline of the
+solver kernel and the CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel.res 1e-8 and HBM GB/s per iter, p-BiCGStab vs BiCGStab, 1 GB300"
+RTOL = 1e-8
+REPLACE_PERIOD = 50
+MAXIT = 20000
+SEED = 0
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
+# x 2 flop x 2.07 GHz (the 2 FMA/clk/SM is NVIDIA's 1.25 TFLOP/s GB300 FP64
+# figure divided by 152 SMs and 2.07 GHz; a DFMA throughput loop measured
+# 1.19 TFLOP/s on this machine).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Oracle iteration counts on this workload (python -m oracle.full_solve_iterations),
+# used to scale the CPU baseline's per-iteration time to a whole solve.
+ORACLE_ITERS = {"pbicgstab_rr50": None, "bicgstab": None}
+# Solver-kernel DRAM traffic per iteration per unknown from an ncu capture of
+# the current kernel source (bytes), or None when not measured for this source.
+TRAFFIC_BYTES_PER_ITER_ROW = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid points per axis")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(n, form="stencil"):
+    N = n ** 3
+    return {"workload": f"3-D convection-diffusion {n}^3 (n={N}), 7-point upwind, velocity "
+                        f"(20 sin y, 20 cos z, 20 sin x), {form} form, FP64, x*~U[-1,1] seed {SEED}, "
+                        f"b=Ax*, x0=0, rtol {RTOL:g}, p-BiCGStab with residual replacement every "
+                        f"{REPLACE_PERIOD} iterations",
+            "n": N, "grid": [n, n, n], "form": form, "replace_period": REPLACE_PERIOD, "rtol": RTOL,
+            "l2": "inputs larger than L2 (each vector 134 MB, working set > 1.6 GB); no flush"}
+
+
+def nnz_of(n):
+    return 7 * n ** 3 - 6 * n ** 2
+
+
+def flops_per_launch(n, info):
+    """Algorithmic FP64 flops of one solve: 2 flops per stored entry per SpMV
+    plus, per iteration and unknown, 13 recurrence FMAs and 8 dot-product
+    FMAs of Algorithm 9 (6 from the paper + ||r|| and ||q||), at 2 flops each."""
+    N = n ** 3
+    return info["spmvs"] * 2.0 * nnz_of(n) + info["iters"] * 2.0 * (13 + 8) * N
+
+
+def bytes_per_iter(n, form="stencil"):
+    """Algorithmic HBM bytes per iteration of Algorithm 9: 23 N-vector passes
+    (phase A reads w r p s z v r0, writes t p s z; phase B reads z x p r s w t
+    r0, writes v x r w), each vector once; plus the matrix per SpMV for CSR
+    (12 bytes per entry + 4 per row pointer)."""
+    N = n ** 3
+    b = 23 * 8 * N
+    if form == "csr":
+        b += 2 * (12 * nnz_of(n) + 4 * (N + 1))
+    return b
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_inputs(n, need_csr):
+    from paper_1612_01395_gb300 import problems as P
+    st = P.cd3d_trig(n)
+    A = P.stencil_to_csr(st) if need_csr else None
+    xs = P.splitmix64_uniform(SEED, n ** 3)
+    return st, A, xs
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------------
+
+def oracle_sample(A, b, method, iters_lo=2, iters_hi=6):
+    """Seconds per oracle iteration and fixed overhead, from two short runs."""
+    import oracle
+    fn = oracle.pbicgstab if method == "pbicgstab" else oracle.bicgstab
+    kw = {"replace_period": REPLACE_PERIOD} if method == "pbicgstab" else {}
+    t = []
+    for k in (iters_lo, iters_hi):
+        t0 = time.perf_counter()
+        fn(A, b, rtol=0.0, maxit=k, fixed_iters=k, **kw)
+        t.append(time.perf_counter() - t0)
+    per_iter = (t[1] - t[0]) / (iters_hi - iters_lo)
+    overhead = max(t[0] - iters_lo * per_iter, 0.0)
+    return per_iter, overhead, t[0] + t[1]
+
+
+def cpu_baseline(A, b, gpu_iters):
+    per_iter, overhead, spent = oracle_sample(A, b, "pbicgstab")
+    iters = ORACLE_ITERS["pbicgstab_rr50"] or gpu_iters
+    src = "oracle's own iteration count" if ORACLE_ITERS["pbicgstab_rr50"] else "the GPU solve's iteration count"
+    return {"value": overhead + iters * per_iter, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"2 and 6 fixed iterations of the FP64 C oracle (Algorithm 9, CSR form) on the full "
+                      f"{A.n}-unknown system ({spent:.1f} s of CPU work), per-iteration time scaled to "
+                      f"{iters} iterations ({src})",
+            "s_per_iter": per_iter}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return 0
+    n = args.n
+    import oracle
+    st, A, xs = build_inputs(n, need_csr=True)
+    b = oracle.spmv(A, xs)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        per_iter, overhead, spent = oracle_sample(A, b, "pbicgstab", 1, 3)
+        iters = ORACLE_ITERS["pbicgstab_rr50"] or 0
+        v = overhead + iters * per_iter if iters else per_iter
+        if s >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    unit = "s" if ORACLE_ITERS["pbicgstab_rr50"] else "s/iter"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(n, "csr"), parallelism="replicas only"),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": "1 and 3 fixed iterations of the FP64 C oracle (Algorithm 9, CSR form) "
+                                       "per step on the full system, per-iteration time scaled to the "
+                                       "oracle's own iteration count"},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------------
+
+def timed_solves(solver, bd, x, steps, method, rr, barrier):
+    """Run `steps` solves bracketed by barrier + synchronize; returns (elapsed s, infos)."""
+    import torch
+    from paper_1612_01395_gb300 import native
+    stream = torch.cuda.current_stream()
+    infos = []
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        x.zero_()
+        if method == "pipelined":
+            st, info = native.pbicgstab_solve(solver.h, bd.data_ptr(), x.data_ptr(), RTOL, MAXIT, rr)
+        else:
+            st, info = native.bicgstab_solve(solver.h, bd.data_ptr(), x.data_ptr(), RTOL, MAXIT)
+        if st != native.PBCG_OK:
+            raise RuntimeError(f"solve failed: {native.STATUS_NAMES.get(st)} {native.pbicgstab_last_error()}")
+        infos.append(info.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1) / 1e3, infos
+
+
+def summarize(elapsed, infos, steps):
+    its = [i["iters"] for i in infos]
+    sec = elapsed / steps
+    return {"value": sec, "iters": int(statistics.median(its)), "ms_per_iter": 1e3 * sec / statistics.median(its),
+            "rel_res_true": max(i["rel_res_true"] for i in infos),
+            "kernel_ms": statistics.mean(i["kernel_ms"] for i in infos),
+            "grid_syncs": infos[0]["grid_syncs"], "spmvs": infos[0]["spmvs"], "grid": infos[0]["grid"]}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+        def barrier():
+            dist.barrier()
+    else:
+        torch.cuda.set_device(0)
+
+        def barrier():
+            pass
+
+    from paper_1612_01395_gb300 import native
+    native.build()
+    n = args.n
+    N = n ** 3
+    want_cpu = (not args.no_cpu_baseline) and rank == 0 and world == 1
+    st, A, xs = build_inputs(n, need_csr=(not args.no_compare) or want_cpu)
+
+    solver = native.Solver.from_stencil(st)
+    xd = torch.from_numpy(xs).cuda()
+    bd = solver.spmv(xd)                       # b = A x* on the device
+    x = torch.zeros_like(bd)
+
+    # warm-up, then the timed region: K pipelined solves, stencil form
+    timed_solves(solver, bd, x, args.warmup, "pipelined", REPLACE_PERIOD, barrier)
+    clocks = ClockSampler(local)
+    clocks.start()
+    elapsed, infos = timed_solves(solver, bd, x, args.steps, "pipelined", REPLACE_PERIOD, barrier)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    main = summarize(elapsed, infos, args.steps)
+    sec = main["value"]
+
+    # roofline of the solver kernel (one cooperative launch per solve)
+    kern_s = main["kernel_ms"] / 1e3
+    fl = flops_per_launch(n, infos[0])
+    achieved_tf = fl / kern_s / 1e12
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    bpi = bytes_per_iter(n)
+    gbs = bpi * main["iters"] / kern_s / 1e9
+    traffic = None
+    if TRAFFIC_BYTES_PER_ITER_ROW is not None:
+        traffic = TRAFFIC_BYTES_PER_ITER_ROW * N * main["iters"]
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "pbicgstab_kernel<StencilOp>",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz",
+                "flops_per_launch": fl,
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                        "peak_source": hbm_src, "bytes_per_iter": bpi}}
+
+    out = {"metric": METRIC, "value": sec, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": dict(workload_config(n), parallelism="replicas only" if world > 1 else "single GPU"),
+           "iters": main["iters"], "ms_per_iter": main["ms_per_iter"], "rel_res_true": main["rel_res_true"],
+           "hbm_gbs_per_iter": gbs, "grid_syncs_per_solve": main["grid_syncs"], "grid": main["grid"],
+           "roofline": roofline, "clocks": clk, "gpu_launches": args.steps}
+
+    # comparison: standard BiCGStab on the same form, and both methods on CSR
+    if not args.no_compare:
+        ksteps = max(1, min(args.steps, 3))
+        _, _ = timed_solves(solver, bd, x, 1, "standard", 0, barrier)
+        el, inf = timed_solves(solver, bd, x, ksteps, "standard", 0, barrier)
+        plain = summarize(el, inf, ksteps)
+        out["bicgstab"] = dict(plain, form="stencil")
+        out["speedup_p_vs_bicgstab"] = plain["value"] / sec
+        csolver = native.Solver.from_csr(A)
+        cmp_csr = {}
+        for method, rr in (("pipelined", REPLACE_PERIOD), ("standard", 0)):
+            timed_solves(csolver, bd, x, 1, method, rr, barrier)
+            el, inf = timed_solves(csolver, bd, x, ksteps, method, rr, barrier)
+            r = summarize(el, inf, ksteps)
+            r["hbm_gbs_per_iter"] = bytes_per_iter(n, "csr") * r["iters"] / (r["kernel_ms"] / 1e3) / 1e9 \
+                if method == "pipelined" else None
+            cmp_csr["pbicgstab" if method == "pipelined" else "bicgstab"] = r
+        out["csr"] = cmp_csr
+        csolver.close()
+
+    # end to end through the host-buffer C entry point: H2D b and x0, solve, D2H x
+    hb = torch.from_numpy(bd.cpu().numpy()).pin_memory()
+    hx = torch.zeros(N, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for s in range(1 + args.steps):
+        hx.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stt, _ = native.pbicgstab_solve_host(solver.h, 0, hb.data_ptr(), hx.data_ptr(), RTOL, MAXIT, REPLACE_PERIOD)
+        t1 = time.perf_counter()
+        if stt != native.PBCG_OK:
+            raise RuntimeError("host solve failed")
+        if s > 0:
+            e2e_times.append(t1 - t0)
+    out["e2e"] = {"value": statistics.median(e2e_times), "unit": "s", "h2d_bytes_per_step": 2 * 8 * N,
+                  "d2h_bytes_per_step": 8 * N + ctypes.sizeof(native.PbcgInfo)}
+
+    if want_cpu:
+        import oracle
+        b_host = oracle.spmv(A, xs)
+        out["cpu_baseline"] = cpu_baseline(A, b_host, main["iters"])
+    else:
+        out["cpu_baseline"] = None
+    solver.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * pbicgstab.h -- C ABI of the GB300 pipelined BiCGStab library.
+ *
+ * Solves A x = b for a real unsymmetric sparse A (CSR or 5/7-point stencil) in
+ * FP64 on one NVIDIA GB300 GPU with
+ *   - pipelined BiCGStab (p-BiCGStab), Cools & Vanroose, arXiv:1612.01395,
+ *     Algorithm 9 (Section 3.3), with the residual replacement of Section 4.2;
+ *   - standard BiCGStab, Algorithm 7 (Section 3.1), for comparison.
+ *
+ * Conventions
+ *   - Pointers named d_* are device pointers (CUDA global memory of the device
+ *     that was current at create); h_* are host pointers. Vectors are dense
+ *     FP64 arrays of length n, indices int32, CSR rows sorted or not.
+ *   - The caller owns every buffer: the matrix, the workspace, b, x and the
+ *     optional history. The library never allocates or frees device memory;
+ *     all scratch lives in the caller's workspace (size from
+ *     pbicgstab_workspace_bytes). Buffers must stay valid while a handle that
+ *     refers to them is in use.
+ *   - Work is enqueued on the stream given at create. A solve returns after its
+ *     result summary (pbcg_info) is on the host: one stream synchronisation per
+ *     solve and none per iteration. Two solves on the same handle must not run
+ *     concurrently (they share the workspace).
+ *   - No call throws; each returns a pbcg_status. pbicgstab_last_error() gives
+ *     a message for the last failing call of the calling thread.
+ *   - Results are deterministic: dot products are reduced in a fixed order, so
+ *     the same inputs on the same GPU give bitwise identical outputs.
+ */
+#ifndef PBICGSTAB_H
+#define PBICGSTAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pbicgstab_s *pbicgstab_t;
+
+typedef enum {
+    PBCG_OK = 0,            /* converged (or ran the requested fixed_iters) */
+    PBCG_NOT_CONVERGED = 1, /* maxit reached before the tolerance */
+    PBCG_BREAKDOWN = 2,     /* zero denominator of alpha, (y,y) = 0 with q != 0,
+                               omega = 0, or (r0, r_{i+1}) = 0; x is the last
+                               full iterate */
+    PBCG_NONFINITE = 3,     /* a reduced scalar is Inf/NaN; x is the last full iterate */
+    PBCG_ERR_ARG = 4,       /* invalid argument (message in pbicgstab_last_error) */
+    PBCG_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+    PBCG_ERR_OOM = 6,       /* workspace too small */
+    PBCG_ERR_TIMEOUT = 7    /* a device-side grid synchronisation exceeded its time
+                               limit; results are invalid, the context stays usable */
+} pbcg_status;
+
+typedef enum { PBCG_PREC_NONE = 0, PBCG_PREC_JACOBI = 1 } pbcg_prec;
+
+/* One stencil coefficient as a function of the grid node (i, j, k):
+ *   c(i,j,k) = (data  ? data [i*stride[0]  + j*stride[1]  + k*stride[2]]  : value)
+ *            + (data2 ? data2[i*stride2[0] + j*stride2[1] + k*stride2[2]] : nothing)
+ * data/data2 are device pointers. A stride of 0 makes the coefficient constant
+ * along that axis, so constants, 1-D/2-D tables and full 3-D fields all fit.
+ * Strides must be >= 0; create rejects a table whose largest index over the
+ * grid is >= its len. */
+typedef struct {
+    double value;
+    const double *data;
+    int64_t stride[3];
+    int64_t len;          /* elements readable at data (every index used must be < len) */
+    const double *data2;
+    int64_t stride2[3];
+    int64_t len2;         /* elements readable at data2 */
+} pbcg_coef;
+
+/* Direction indices of pbcg_stencil.coef. */
+enum { PBCG_C = 0, PBCG_W = 1, PBCG_E = 2, PBCG_S = 3, PBCG_N = 4, PBCG_B = 5, PBCG_T = 6 };
+
+/* A 5-point (nz == 1) or 7-point stencil on an nx x ny x nz grid, rows ordered
+ * lexicographically with x fastest: row = i + nx*(j + ny*k). Row `row` of A has
+ * coef[C] on the diagonal and coef[W]/[E] at columns row -/+ 1, coef[S]/[N] at
+ * row -/+ nx, coef[B]/[T] at row -/+ nx*ny, each evaluated at the row's node;
+ * neighbours outside the grid are dropped (Dirichlet elimination). A row is
+ * summed in the order B, S, W, C, E, N, T (ascending column), which makes the
+ * stencil and the equivalent sorted CSR give identical products. */
+typedef struct {
+    int32_t nx, ny, nz;
+    pbcg_coef coef[7];
+} pbcg_stencil;
+
+/* Per-solve options; pass NULL for the defaults shown. */
+typedef struct {
+    int32_t max_replacements; /* cap on residual replacements, -1 = unlimited (default -1) */
+    int32_t fixed_iters;      /* > 0: run exactly this many iterations and ignore rtol
+                                 (breakdown still stops); for step-by-step comparison (default 0) */
+    double *d_history;        /* NULL, or device buffer of (fixed_iters>0 ? fixed_iters : maxit)+1
+                                 doubles: ||r_i||_2 of the recursive residual, i = 0..iters;
+                                 entries past iters are untouched (default NULL) */
+    int32_t plain_variant;    /* bicgstab_solve only: 0 = automatic, 3 = three grid-wide
+                                 synchronisations per iteration with neighbour values of p and
+                                 q formed on the fly, 5 = five synchronisations and fewer FP64
+                                 operations (default 0) */
+    int32_t grid;             /* 0 = automatic; > 0 forces the number of thread blocks
+                                 (clamped to what can be co-resident) (default 0) */
+} pbcg_opts;
+
+/* Result summary, written to host memory by every solve. */
+typedef struct {
+    int32_t iters;            /* iterations performed; a final half step counts as one */
+    int32_t status;           /* pbcg_status of the solve */
+    int32_t half_step;        /* 1 if it stopped at x_i + alpha_i p_i because ||q_i|| <= tol */
+    int32_t n_replacements;   /* residual replacement steps performed */
+    double nr0;               /* ||r_0||_2 = ||b - A x_0||_2 */
+    double rel_res_recursive; /* ||r_iters||_2 / ||r_0||_2 (recursive residual) */
+    double rel_res_true;      /* ||b - A x||_2 / ||r_0||_2, computed after the loop */
+    int32_t grid;             /* thread blocks used */
+    int32_t block;            /* threads per block */
+    int32_t grid_syncs;       /* device-wide synchronisations performed */
+    int32_t spmvs;            /* sparse matrix-vector products performed */
+    float kernel_ms;          /* duration of the solver kernel, CUDA events on the handle's stream */
+    int32_t pad;
+} pbcg_info;
+
+/* Bytes of device workspace a handle for n unknowns needs (256-byte aligned
+ * start required). Covers 12 FP64 vectors of length n and a control block. */
+size_t pbicgstab_workspace_bytes(int32_t n);
+
+/* Create a handle for a CSR matrix (Section 3: A general sparse, unsymmetric).
+ *   n, nnz         size; 0 <= n, 0 <= nnz < 2^31
+ *   d_rowptr[n+1]  row offsets (d_rowptr[0] == 0, non-decreasing, d_rowptr[n] == nnz)
+ *   d_col[nnz]     column indices in [0, n)
+ *   d_val[nnz]     values
+ *   prec           PBCG_PREC_NONE (PBCG_PREC_JACOBI returns PBCG_ERR_ARG: not built yet)
+ *   d_workspace    caller-owned, >= pbicgstab_workspace_bytes(n) bytes, 256-byte aligned
+ *   stream         a cudaStream_t (NULL = legacy default stream)
+ * The structure is validated on the device (one synchronisation); an invalid
+ * matrix returns PBCG_ERR_ARG and no handle. */
+pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr, const int32_t *d_col,
+                                 const double *d_val, pbcg_prec prec, void *d_workspace, size_t ws_bytes,
+                                 void *stream, pbicgstab_t *out);
+
+/* Create a handle for a stencil operator (Section 5, PTP1/PTP2 are such
+ * stencils). desc is copied; its coefficient tables must stay valid. */
+pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, void *d_workspace,
+                                     size_t ws_bytes, void *stream, pbicgstab_t *out);
+
+/* Pipelined BiCGStab, Algorithm 9, with residual replacement (Section 4.2).
+ *   d_b[n]           right-hand side
+ *   d_x[n]           in: x_0; out: the last iterate
+ *   rtol             stop when ||r_i||_2 <= rtol * ||r_0||_2 on the recursive residual
+ *   maxit            iteration cap (>= 0)
+ *   replace_period   k > 0: replace r, w, s, z by their true values every k
+ *                    iterations (r := b - A x and w := A r before the second
+ *                    reduction of iteration i-1, s := A p and z := A s after p_i
+ *                    in iteration i, for i mod k == 0); 0 disables
+ *   opts             NULL or options
+ *   info             host pointer, filled on return (also on failure when possible)
+ * Returns info->status, or an error code. */
+pbcg_status pbicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
+                            int32_t replace_period, const pbcg_opts *opts, pbcg_info *info);
+
+/* Standard BiCGStab, Algorithm 7, on the same handle and workspace. Arguments
+ * as pbicgstab_solve without replacement. */
+pbcg_status bicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
+                           const pbcg_opts *opts, pbcg_info *info);
+
+/* pbicgstab_solve on HOST buffers: copies h_b and h_x (x_0) to the workspace,
+ * solves, and copies the iterate back into h_x; all on the handle's stream.
+ * Page-locked host buffers give the fastest copies. method: 0 = pipelined
+ * (Algorithm 9), 1 = standard (Algorithm 7, replace_period ignored). */
+pbcg_status pbicgstab_solve_host(pbicgstab_t h, int32_t method, const double *h_b, double *h_x, double rtol,
+                                 int32_t maxit, int32_t replace_period, const pbcg_opts *opts, pbcg_info *info);
+
+/* y = A x with the handle's operator (the SpMV building block, Section 1).
+ * Asynchronous on the handle's stream; d_x and d_y must not overlap. */
+pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y);
+
+/* Number of unknowns of the handle. */
+int32_t pbicgstab_size(pbicgstab_t h);
+
+/* Release the handle (host memory only; the caller's buffers are untouched).
+ * Synchronises the handle's stream first. NULL is ignored. */
+void pbicgstab_destroy(pbicgstab_t h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *pbicgstab_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBICGSTAB_H */

@@ -1,0 +1,91 @@
+// The sparse operators A of A x = b: CSR and 5/7-point stencil.
+//
+// Each operator computes one row of a product, (A u)_row = sum_j a_{row,j} u_j,
+// where u_j is produced by a loader functor. The plain loader reads a vector;
+// other loaders form a vector on the fly (e.g. p = r + beta (p - omega s) for
+// neighbours), which lets a solver phase fuse an AXPY into its SpMV.
+//
+// Summation order of a row: its stored entries in order (CSR); B, S, W, C, E,
+// N, T (stencil) -- ascending column index, so a stencil and its sorted CSR
+// assembly give bitwise identical rows. Products are accumulated with FMA.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace pbcg {
+
+// u_j = x[j]
+struct VecLoad {
+    const double *x;
+    __device__ __forceinline__ double operator()(int j) const { return x[j]; }
+};
+
+// u_j = r_j + beta (p_j - omega s_j): the p-recurrence of Algorithm 7
+struct PLoad {
+    const double *r, *p, *s;
+    double beta, omega;
+    __device__ __forceinline__ double operator()(int j) const { return fma(beta, fma(-omega, s[j], p[j]), r[j]); }
+};
+
+// u_j = r_j - alpha s_j: q of Algorithm 7
+struct QLoad {
+    const double *r, *s;
+    double alpha;
+    __device__ __forceinline__ double operator()(int j) const { return fma(-alpha, s[j], r[j]); }
+};
+
+struct CsrOp {
+    int n;
+    const int *__restrict__ rowptr;
+    const int *__restrict__ col;
+    const double *__restrict__ val;
+
+    template <class L>
+    __device__ __forceinline__ double row(int r, const L &u) const {
+        const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+        double acc = 0.0;
+        for (int k = b; k < e; ++k) acc = fma(__ldg(val + k), u(__ldg(col + k)), acc);
+        return acc;
+    }
+};
+
+struct StCoef {
+    double value;
+    const double *t1;
+    long long a1, b1, c1;
+    const double *t2;
+    long long a2, b2, c2;
+};
+
+struct StencilOp {
+    int n, nx, ny, nz;
+    int nxy;
+    FastDiv dx, dy;
+    StCoef c[7];   // C, W, E, S, N, B, T
+
+    __device__ __forceinline__ double coef(int d, int i, int j, int k) const {
+        const StCoef &q = c[d];
+        double v = q.t1 ? __ldg(q.t1 + (i * q.a1 + j * q.b1 + k * q.c1)) : q.value;
+        if (q.t2) v = __dadd_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
+        return v;
+    }
+
+    template <class L>
+    __device__ __forceinline__ double row(int r, const L &u) const {
+        const int t = (int)dx.div((uint32_t)r);
+        const int i = r - t * nx;
+        const int k = (int)dy.div((uint32_t)t);
+        const int j = t - k * ny;
+        double acc = 0.0;
+        if (k > 0) acc = fma(coef(PBCG_B, i, j, k), u(r - nxy), acc);
+        if (j > 0) acc = fma(coef(PBCG_S, i, j, k), u(r - nx), acc);
+        if (i > 0) acc = fma(coef(PBCG_W, i, j, k), u(r - 1), acc);
+        acc = fma(coef(PBCG_C, i, j, k), u(r), acc);
+        if (i < nx - 1) acc = fma(coef(PBCG_E, i, j, k), u(r + 1), acc);
+        if (j < ny - 1) acc = fma(coef(PBCG_N, i, j, k), u(r + nx), acc);
+        if (k < nz - 1) acc = fma(coef(PBCG_T, i, j, k), u(r + nxy), acc);
+        return acc;
+    }
+};
+
+}  // namespace pbcg

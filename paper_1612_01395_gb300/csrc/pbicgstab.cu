@@ -1,0 +1,341 @@
+// C ABI of the library (declared in include/pbicgstab.h): argument checks,
+// workspace layout, launch-shape choice and the cooperative launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pbicgstab.h"
+#include "solvers.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pbcg_status fail(pbcg_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define PBCG_CUDA(call)                                                                                  \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return fail(PBCG_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kVectors = 12;   // r r0 p s z q y w t v + host staging b, x
+
+size_t vec_stride(int32_t n) { return ((size_t)(n > 0 ? n : 1) + 31) / 32 * 32; }   // doubles
+
+}  // namespace
+
+struct pbicgstab_s {
+    int kind;   // 0 = CSR, 1 = stencil
+    pbcg::CsrOp csr;
+    pbcg::StencilOp st;
+    int n;
+    char *ws;
+    cudaStream_t stream;
+    int device, num_sms;
+    int occ_pipe, occ_plain;   // co-resident blocks per SM of each solver kernel
+    pbcg::Vectors V;
+    double *b_stage, *x_stage;
+    pbcg::Control *ctl;
+    double *partials;
+    cudaEvent_t ev0, ev1;   // bracket the solver kernel
+};
+
+extern "C" {
+
+size_t pbicgstab_workspace_bytes(int32_t n) {
+    if (n < 0) return 0;
+    return pbcg::kControlBytes + pbcg::kPartialBytes + (size_t)kVectors * vec_stride(n) * sizeof(double);
+}
+
+const char *pbicgstab_last_error(void) { return g_err; }
+
+int32_t pbicgstab_size(pbicgstab_t h) { return h ? h->n : -1; }
+
+}  // extern "C"
+
+namespace {
+
+template <class Op>
+pbcg_status occupancy(int *pipe, int *plain) {
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(pipe, pbcg::pbicgstab_kernel<Op>, pbcg::kTPB, 0));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(plain, pbcg::bicgstab_kernel<Op>, pbcg::kTPB, 0));
+    if (*pipe < 1 || *plain < 1) return fail(PBCG_ERR_CUDA, "solver kernel cannot be resident on an SM");
+    return PBCG_OK;
+}
+
+pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, size_t ws_bytes, void *stream) {
+    if (prec != PBCG_PREC_NONE)
+        return fail(PBCG_ERR_ARG, "preconditioner %d is not available (only PBCG_PREC_NONE)", (int)prec);
+    if (!d_ws) return fail(PBCG_ERR_ARG, "workspace is NULL");
+    if (((uintptr_t)d_ws) % kAlign) return fail(PBCG_ERR_ARG, "workspace must be 256-byte aligned");
+    const size_t need = pbicgstab_workspace_bytes(n);
+    if (ws_bytes < need) return fail(PBCG_ERR_OOM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    h->n = n;
+    h->ws = (char *)d_ws;
+    h->stream = (cudaStream_t)stream;
+    PBCG_CUDA(cudaGetDevice(&h->device));
+    PBCG_CUDA(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    int coop = 0;
+    PBCG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
+    if (!coop) return fail(PBCG_ERR_CUDA, "device does not support cooperative launches");
+    PBCG_CUDA(cudaEventCreate(&h->ev0));
+    PBCG_CUDA(cudaEventCreate(&h->ev1));
+    h->ctl = (pbcg::Control *)h->ws;
+    h->partials = (double *)(h->ws + pbcg::kControlBytes);
+    double *v0 = (double *)(h->ws + pbcg::kControlBytes + pbcg::kPartialBytes);
+    const size_t s = vec_stride(n);
+    double **slots[kVectors] = {&h->V.r, &h->V.r0, &h->V.p, &h->V.s, &h->V.z, &h->V.q,
+                                &h->V.y, &h->V.w, &h->V.t, &h->V.v, &h->b_stage, &h->x_stage};
+    for (int k = 0; k < kVectors; ++k) *slots[k] = v0 + (size_t)k * s;
+    return PBCG_OK;
+}
+
+// Largest table index a strided coefficient reaches over the grid.
+long long max_index(const int64_t st[3], int nx, int ny, int nz) {
+    return st[0] * (long long)(nx - 1) + st[1] * (long long)(ny - 1) + st[2] * (long long)(nz - 1);
+}
+
+int pick_grid(const pbicgstab_s *h, int occ, int req) {
+    int max_grid = occ * h->num_sms;
+    if (max_grid > pbcg::kMaxGrid) max_grid = pbcg::kMaxGrid;
+    if (req > 0) return req < max_grid ? req : max_grid;
+    // at least 32 rows per block; all co-resident blocks for large n
+    long long want = ((long long)h->n + 31) / 32;
+    if (want < 1) want = 1;
+    return (int)(want < max_grid ? want : max_grid);
+}
+
+template <class Op>
+pbcg_status launch_solver(pbicgstab_s *h, const Op &op, bool pipelined, const pbcg::SolveArgs &args, int grid) {
+    void *params[2] = {(void *)&op, (void *)&args};
+    const void *fn = pipelined ? (const void *)pbcg::pbicgstab_kernel<Op> : (const void *)pbcg::bicgstab_kernel<Op>;
+    PBCG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(pbcg::kTPB), params, 0, h->stream));
+    return PBCG_OK;
+}
+
+pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double *d_x, double rtol, int32_t maxit,
+                      int32_t replace_period, const pbcg_opts *opts, pbcg_info *info) {
+    if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
+    if (info) memset(info, 0, sizeof(*info));
+    if (h->n > 0 && (!d_b || !d_x)) return fail(PBCG_ERR_ARG, "b or x is NULL");
+    if (!(rtol >= 0.0)) return fail(PBCG_ERR_ARG, "rtol must be >= 0");
+    if (maxit < 0) return fail(PBCG_ERR_ARG, "maxit must be >= 0");
+    if (replace_period < 0) return fail(PBCG_ERR_ARG, "replace_period must be >= 0");
+    pbcg_opts o{-1, 0, nullptr, 0, 0};
+    if (opts) o = *opts;
+    if (o.fixed_iters < 0) return fail(PBCG_ERR_ARG, "fixed_iters must be >= 0");
+    if (o.plain_variant != 0 && o.plain_variant != 3 && o.plain_variant != 5)
+        return fail(PBCG_ERR_ARG, "plain_variant must be 0, 3 or 5");
+    if (o.grid < 0) return fail(PBCG_ERR_ARG, "grid must be >= 0");
+
+    pbcg::SolveArgs a;
+    a.n = h->n;
+    a.b = d_b;
+    a.x = d_x;
+    a.V = h->V;
+    a.ctl = h->ctl;
+    a.partials = h->partials;
+    a.hist = o.d_history;
+    a.rtol = rtol;
+    a.fixed = o.fixed_iters > 0 ? 1 : 0;
+    a.limit = o.fixed_iters > 0 ? o.fixed_iters : maxit;
+    a.replace_period = pipelined ? replace_period : 0;
+    a.max_repl = o.max_replacements;
+    // Variant 3 saves two grid synchronisations per iteration at the price of
+    // 18 more FP64 operations per row; at ~1.9 FP64 FMA/clk/SM and ~1.4 us per
+    // synchronisation the two break even near n = 1e5.
+    a.variant = o.plain_variant ? o.plain_variant : (h->n < 100000 ? 3 : 5);
+
+    const int grid = pick_grid(h, pipelined ? h->occ_pipe : h->occ_plain, o.grid);
+    PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
+    PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
+    if (h->n > 0) {
+        pbcg_status st = h->kind == 0 ? launch_solver(h, h->csr, pipelined, a, grid)
+                                      : launch_solver(h, h->st, pipelined, a, grid);
+        if (st != PBCG_OK) return st;
+    }
+    PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
+    pbcg::Control c;
+    PBCG_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    PBCG_CUDA(cudaStreamSynchronize(h->stream));
+    pbcg_status st;
+    if (h->n == 0) {
+        c.status = PBCG_OK;
+        c.iters = 0;
+    }
+    if (c.abort != 0) {
+        st = fail((pbcg_status)c.abort, "solver aborted: a grid-wide synchronisation timed out");
+        c.status = c.abort;
+    } else {
+        st = (pbcg_status)c.status;
+    }
+    if (info) {
+        info->iters = c.iters;
+        info->status = c.status;
+        info->half_step = c.half_step;
+        info->n_replacements = c.n_repl;
+        info->nr0 = c.nr0;
+        info->rel_res_recursive = c.rel_rec;
+        info->rel_res_true = c.rel_true;
+        info->grid = h->n > 0 ? grid : 0;
+        info->block = pbcg::kTPB;
+        info->grid_syncs = c.grid_syncs;
+        info->spmvs = c.spmvs;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) info->kernel_ms = ms;
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr, const int32_t *d_col,
+                                 const double *d_val, pbcg_prec prec, void *d_workspace, size_t ws_bytes,
+                                 void *stream, pbicgstab_t *out) {
+    if (!out) return fail(PBCG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || nnz < 0) return fail(PBCG_ERR_ARG, "n and nnz must be >= 0");
+    if (!d_rowptr || (nnz > 0 && (!d_col || !d_val))) return fail(PBCG_ERR_ARG, "CSR array is NULL");
+    pbicgstab_s *h = new (std::nothrow) pbicgstab_s();
+    if (!h) return fail(PBCG_ERR_OOM, "host allocation failed");
+    pbcg_status st = common_init(h, n, prec, d_workspace, ws_bytes, stream);
+    if (st == PBCG_OK) {
+        h->kind = 0;
+        h->csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        st = occupancy<pbcg::CsrOp>(&h->occ_pipe, &h->occ_plain);
+    }
+    if (st == PBCG_OK) {
+        // structure check on the device; the flag lives in the control block
+        int *flag = &h->ctl->abort;
+        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
+        if (e == cudaSuccess) {
+            int blocks = (int)(((long long)(nnz > n ? nnz : n) + 1 + 255) / 256);
+            if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+            if (blocks < 1) blocks = 1;
+            pbcg::csr_check_kernel<<<blocks, 256, 0, h->stream>>>(n, nnz, d_rowptr, d_col, flag);
+            e = cudaGetLastError();
+        }
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = fail(PBCG_ERR_CUDA, "CSR check: %s", cudaGetErrorString(e));
+        else if (bad) st = fail(PBCG_ERR_ARG, "invalid CSR structure (check code %d)", bad);
+    }
+    if (st != PBCG_OK) {
+        pbicgstab_destroy(h);
+        return st;
+    }
+    *out = h;
+    return PBCG_OK;
+}
+
+pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, void *d_workspace, size_t ws_bytes,
+                                     void *stream, pbicgstab_t *out) {
+    if (!out) return fail(PBCG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(PBCG_ERR_ARG, "stencil descriptor is NULL");
+    const int nx = desc->nx, ny = desc->ny, nz = desc->nz;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(PBCG_ERR_ARG, "grid dimensions must be >= 1");
+    const long long nn = (long long)nx * ny * nz;
+    if (nn >= (1ll << 31)) return fail(PBCG_ERR_ARG, "grid has more than 2^31-1 nodes");
+    for (int d = 0; d < 7; ++d) {
+        const pbcg_coef &c = desc->coef[d];
+        for (int k = 0; k < 3; ++k)
+            if (c.stride[k] < 0 || c.stride2[k] < 0) return fail(PBCG_ERR_ARG, "coefficient %d: negative stride", d);
+        if (c.data && max_index(c.stride, nx, ny, nz) >= c.len)
+            return fail(PBCG_ERR_ARG, "coefficient %d: table too short (len %lld)", d, (long long)c.len);
+        if (c.data2 && max_index(c.stride2, nx, ny, nz) >= c.len2)
+            return fail(PBCG_ERR_ARG, "coefficient %d: second table too short (len %lld)", d, (long long)c.len2);
+    }
+    pbicgstab_s *h = new (std::nothrow) pbicgstab_s();
+    if (!h) return fail(PBCG_ERR_OOM, "host allocation failed");
+    pbcg_status st = common_init(h, (int32_t)nn, prec, d_workspace, ws_bytes, stream);
+    if (st == PBCG_OK) {
+        h->kind = 1;
+        pbcg::StencilOp &o = h->st;
+        o.n = (int)nn;
+        o.nx = nx;
+        o.ny = ny;
+        o.nz = nz;
+        o.nxy = nx * ny;
+        o.dx.init((uint32_t)nx);
+        o.dy.init((uint32_t)ny);
+        for (int d = 0; d < 7; ++d) {
+            const pbcg_coef &c = desc->coef[d];
+            o.c[d] = pbcg::StCoef{c.value, c.data, c.stride[0], c.stride[1], c.stride[2],
+                                  c.data2, c.stride2[0], c.stride2[1], c.stride2[2]};
+        }
+        st = occupancy<pbcg::StencilOp>(&h->occ_pipe, &h->occ_plain);
+    }
+    if (st != PBCG_OK) {
+        pbicgstab_destroy(h);
+        return st;
+    }
+    *out = h;
+    return PBCG_OK;
+}
+
+pbcg_status pbicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
+                            int32_t replace_period, const pbcg_opts *opts, pbcg_info *info) {
+    return run_solve(h, true, d_b, d_x, rtol, maxit, replace_period, opts, info);
+}
+
+pbcg_status bicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
+                           const pbcg_opts *opts, pbcg_info *info) {
+    return run_solve(h, false, d_b, d_x, rtol, maxit, 0, opts, info);
+}
+
+pbcg_status pbicgstab_solve_host(pbicgstab_t h, int32_t method, const double *h_b, double *h_x, double rtol,
+                                 int32_t maxit, int32_t replace_period, const pbcg_opts *opts, pbcg_info *info) {
+    if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
+    if (method != 0 && method != 1) return fail(PBCG_ERR_ARG, "method must be 0 (pipelined) or 1 (standard)");
+    if (h->n > 0 && (!h_b || !h_x)) return fail(PBCG_ERR_ARG, "b or x is NULL");
+    const size_t bytes = (size_t)h->n * sizeof(double);
+    if (bytes) {
+        PBCG_CUDA(cudaMemcpyAsync(h->b_stage, h_b, bytes, cudaMemcpyHostToDevice, h->stream));
+        PBCG_CUDA(cudaMemcpyAsync(h->x_stage, h_x, bytes, cudaMemcpyHostToDevice, h->stream));
+    }
+    pbcg_status st = run_solve(h, method == 0, h->b_stage, h->x_stage, rtol, maxit, replace_period, opts, info);
+    if (st == PBCG_ERR_ARG || st == PBCG_ERR_CUDA || st == PBCG_ERR_OOM) return st;
+    if (bytes) {
+        PBCG_CUDA(cudaMemcpyAsync(h_x, h->x_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+        PBCG_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return st;
+}
+
+pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y) {
+    if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
+    if (h->n == 0) return PBCG_OK;
+    if (!d_x || !d_y) return fail(PBCG_ERR_ARG, "x or y is NULL");
+    if ((d_x < d_y + h->n) && (d_y < d_x + h->n)) return fail(PBCG_ERR_ARG, "x and y overlap");
+    int blocks = (h->n + pbcg::kTPB - 1) / pbcg::kTPB;
+    if (blocks > 16 * h->num_sms) blocks = 16 * h->num_sms;
+    if (h->kind == 0)
+        pbcg::spmv_kernel<<<blocks, pbcg::kTPB, 0, h->stream>>>(h->csr, d_x, d_y);
+    else
+        pbcg::spmv_kernel<<<blocks, pbcg::kTPB, 0, h->stream>>>(h->st, d_x, d_y);
+    PBCG_CUDA(cudaGetLastError());
+    return PBCG_OK;
+}
+
+void pbicgstab_destroy(pbicgstab_t h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,448 @@
+// Persistent cooperative solver kernels: one launch runs a whole solve.
+//
+// Rows are split into gridDim.x contiguous ranges, one per thread block, and a
+// thread owns the rows lo + threadIdx.x + m * kTPB of its block's range in
+// every phase. A phase is one sweep over the rows that fuses an SpMV, the
+// AXPY recurrences that consume it and the partial dot products of a
+// reduction; phases are separated by grid_sum / grid_sync. Every block then
+// holds the same reduced scalars (alpha, beta, omega, rho), so the scalars
+// never leave the GPU and the host is not involved between iterations.
+//
+// Pipelined BiCGStab (Algorithm 9) takes 2 grid-wide synchronisations per
+// iteration: on one GPU the SpMV of each phase needs its input vector complete
+// across the grid, and that same synchronisation completes the reduction whose
+// scalar the phase consumes -- the two reductions of Algorithm 9 ride on the
+// two synchronisations its SpMVs need anyway. Standard BiCGStab (Algorithm 7)
+// needs 3 (variant 3: neighbour values of p and q are formed on the fly inside
+// the SpMV) or 5 (variant 5: p and q are written first, fewer FP64 operations).
+#pragma once
+
+#include "operators.cuh"
+
+namespace pbcg {
+
+struct Vectors {
+    double *r, *r0, *p, *s, *z, *q, *y, *w, *t, *v;
+};
+
+struct SolveArgs {
+    int n;
+    const double *b;
+    double *x;
+    Vectors V;
+    Control *ctl;
+    double *partials;
+    double *hist;       // nullable
+    double rtol;
+    int limit;          // iterations allowed (maxit or fixed_iters)
+    int fixed;          // 1: ignore rtol
+    int replace_period;
+    int max_repl;       // < 0: unlimited
+    int variant;        // Algorithm 7 only: 3 or 5
+};
+
+struct Outcome {
+    int iters, status, half, nrr;
+    double nr0, nr;
+};
+
+__device__ __forceinline__ bool all_finite(const double *v, int k) {
+    for (int i = 0; i < k; ++i)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+#define PBCG_ROWS(i) for (int i = lo + (int)threadIdx.x; i < hi; i += kTPB)
+
+// Final true residual ||b - A x|| and the result record (block 0).
+template <class Op>
+__device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32], int *sflag,
+                                       int lo, int hi, const Outcome &o, int spmvs) {
+    double d[1] = {0.0};
+    PBCG_ROWS(i) {
+        const double res = a.b[i] - A.row(i, VecLoad{a.x});
+        d[0] = fma(res, res, d[0]);
+    }
+    if (!grid_sum<1>(g, d, sm, sflag)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Control *c = a.ctl;
+        const double nt = sqrt(d[0]);
+        c->iters = o.iters;
+        c->status = o.status;
+        c->half_step = o.half;
+        c->n_repl = o.nrr;
+        c->grid_syncs = g.count;
+        c->spmvs = spmvs + 1;
+        c->nr0 = o.nr0;
+        c->rel_rec = o.nr0 > 0.0 ? o.nr / o.nr0 : 0.0;
+        c->rel_true = o.nr0 > 0.0 ? nt / o.nr0 : nt;
+    }
+}
+
+// ===========================================================================
+// Algorithm 9 (pipelined BiCGStab) with the residual replacement of
+// Section 4.2 (r := b - A x, w := A r before the second reduction of iteration
+// i-1; s := A p, z := A s after p_i; for i mod k == 0).
+// ===========================================================================
+template <class Op>
+__device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+                                               int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
+    const Vectors V = a.V;
+    double *x = a.x;
+    const bool fixed = a.fixed != 0;
+
+    // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
+    double d0[1] = {0.0};
+    PBCG_ROWS(i) {
+        const double ri = a.b[i] - A.row(i, VecLoad{x});
+        V.r[i] = ri;
+        V.r0[i] = ri;
+        V.p[i] = 0.0;
+        V.s[i] = 0.0;
+        V.z[i] = 0.0;
+        V.v[i] = 0.0;
+        d0[0] = fma(ri, ri, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    double rho = d0[0];                 // (r0, r_0)
+    o.nr0 = sqrt(rho);
+    o.nr = o.nr0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
+    const double tol = __dmul_rn(a.rtol, o.nr0);
+    if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
+
+    // w_0 := A r_0; alpha_0 := (r0, r0) / (r0, w0)
+    d0[0] = 0.0;
+    PBCG_ROWS(i) {
+        const double wi = A.row(i, VecLoad{V.r});
+        V.w[i] = wi;
+        d0[0] = fma(V.r0[i], wi, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    if (!isfinite(d0[0])) { o.status = PBCG_NONFINITE; return true; }
+    if (d0[0] == 0.0) { o.status = PBCG_BREAKDOWN; return true; }
+    double alpha = __ddiv_rn(rho, d0[0]), beta = 0.0, omega = 0.0;
+
+    bool replaced_rw = false;   // r_i, w_i were replaced at the end of iteration i-1
+    int it = 0;
+    while (it < a.limit) {
+        // ---- phase A: t_i = A w_i; p_i, s_i, z_i, q_i, y_i; first reduction
+        double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
+        if (!replaced_rw) {
+            PBCG_ROWS(i) {
+                const double ti = A.row(i, VecLoad{V.w});
+                const double ri = V.r[i], wi = V.w[i], si = V.s[i], zi = V.z[i];
+                const double pn = fma(beta, fma(-omega, si, V.p[i]), ri);   // p_i
+                const double sn = fma(beta, fma(-omega, zi, si), wi);       // s_i, eq. (1)
+                const double zn = fma(beta, fma(-omega, V.v[i], zi), ti);   // z_i, eq. (6)
+                const double qi = fma(-alpha, sn, ri);                      // q_i
+                const double yi = fma(-alpha, zn, wi);                      // y_i, eq. (4)
+                V.t[i] = ti;
+                V.p[i] = pn;
+                V.s[i] = sn;
+                V.z[i] = zn;
+                V.q[i] = qi;
+                V.y[i] = yi;
+                const double r0i = V.r0[i];
+                d1[0] = fma(qi, yi, d1[0]);
+                d1[1] = fma(yi, yi, d1[1]);
+                d1[2] = fma(qi, qi, d1[2]);
+                d1[3] = fma(r0i, sn, d1[3]);
+                d1[4] = fma(r0i, zn, d1[4]);
+            }
+            ++spmvs;
+        } else {
+            // replacement, second part: t_i = A w_i (w_i replaced), p_i; then s_i := A p_i; z_i := A s_i
+            PBCG_ROWS(i) {
+                V.t[i] = A.row(i, VecLoad{V.w});
+                V.p[i] = fma(beta, fma(-omega, V.s[i], V.p[i]), V.r[i]);
+            }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) { V.s[i] = A.row(i, VecLoad{V.p}); }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double zn = A.row(i, VecLoad{V.s});
+                const double sn = V.s[i], ri = V.r[i], wi = V.w[i];
+                const double qi = fma(-alpha, sn, ri);
+                const double yi = fma(-alpha, zn, wi);
+                V.z[i] = zn;
+                V.q[i] = qi;
+                V.y[i] = yi;
+                const double r0i = V.r0[i];
+                d1[0] = fma(qi, yi, d1[0]);
+                d1[1] = fma(yi, yi, d1[1]);
+                d1[2] = fma(qi, qi, d1[2]);
+                d1[3] = fma(r0i, sn, d1[3]);
+                d1[4] = fma(r0i, zn, d1[4]);
+            }
+            spmvs += 3;
+        }
+        if (!grid_sum<5>(g, d1, sm, sflag)) return false;
+        const double qy = d1[0], yy = d1[1], qq = d1[2], r0s = d1[3], r0z = d1[4];
+        if (!all_finite(d1, 5)) { o.status = PBCG_NONFINITE; break; }
+        const double nq = sqrt(qq);
+        const bool small_q = !fixed && nq <= tol;
+        if (small_q || yy == 0.0) {
+            if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
+            PBCG_ROWS(i) { x[i] = fma(alpha, V.p[i], x[i]); }   // half step x_i + alpha_i p_i
+            if (!grid_sync(g, sflag)) return false;
+            ++it;
+            o.nr = nq;
+            o.half = 1;
+            o.status = PBCG_OK;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = nq;
+            break;
+        }
+        omega = __ddiv_rn(qy, yy);
+        if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+
+        // ---- phase B: v_i = A z_i; x_{i+1}, r_{i+1}, w_{i+1}; second reduction
+        const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
+                                 (a.max_repl < 0 || o.nrr < a.max_repl);
+        double d2[3] = {0.0, 0.0, 0.0};   // (r0,r) (r0,w) (r,r)
+        if (!replace_now) {
+            PBCG_ROWS(i) {
+                const double vi = A.row(i, VecLoad{V.z});
+                const double qi = V.q[i], yi = V.y[i];
+                x[i] = fma(omega, qi, fma(alpha, V.p[i], x[i]));
+                const double rn = fma(-omega, yi, qi);                        // eq. (7)
+                const double wn = fma(-omega, fma(-alpha, vi, V.t[i]), yi);   // eq. (8)
+                V.v[i] = vi;
+                V.r[i] = rn;
+                V.w[i] = wn;
+                const double r0i = V.r0[i];
+                d2[0] = fma(r0i, rn, d2[0]);
+                d2[1] = fma(r0i, wn, d2[1]);
+                d2[2] = fma(rn, rn, d2[2]);
+            }
+            ++spmvs;
+        } else {
+            // replacement, first part: x_{i+1}; r_{i+1} := b - A x_{i+1}; w_{i+1} := A r_{i+1}
+            PBCG_ROWS(i) { x[i] = fma(omega, V.q[i], fma(alpha, V.p[i], x[i])); }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) { V.r[i] = a.b[i] - A.row(i, VecLoad{x}); }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double wn = A.row(i, VecLoad{V.r});
+                const double rn = V.r[i], r0i = V.r0[i];
+                V.w[i] = wn;
+                d2[0] = fma(r0i, rn, d2[0]);
+                d2[1] = fma(r0i, wn, d2[1]);
+                d2[2] = fma(rn, rn, d2[2]);
+            }
+            spmvs += 2;
+            o.nrr++;
+        }
+        replaced_rw = replace_now;
+        if (!grid_sum<3>(g, d2, sm, sflag)) return false;
+        ++it;
+        const double rho_n = d2[0], r0w = d2[1];
+        o.nr = sqrt(d2[2]);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = o.nr;
+        if (!all_finite(d2, 3)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && o.nr <= tol) { o.status = PBCG_OK; break; }
+        if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        // beta_i = (alpha_i / omega_i) (r0, r_{i+1}) / (r0, r_i); alpha_{i+1} by eq. (3)
+        beta = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_n, rho));
+        const double den = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
+        if (den == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        alpha = __ddiv_rn(rho_n, den);
+        rho = rho_n;
+    }
+    o.iters = it;
+    if (it == a.limit && o.status == PBCG_NOT_CONVERGED && fixed) o.status = PBCG_OK;
+    return true;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kTPB) pbicgstab_kernel(const Op A, const SolveArgs a) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ int sflag;
+    GridSync g{a.ctl, a.partials, 0u, 0};
+    const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
+    const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
+    Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+    int spmvs = 0;
+    if (!pipelined_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
+    finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+}
+
+// ===========================================================================
+// Algorithm 7 (standard BiCGStab). p and s use two buffers each in variant 3:
+// the phase that forms p_i for its SpMV reads p_{i-1}, s_{i-1} of neighbours
+// while writing p_i, s_i, so the old and new values must not share storage.
+// ===========================================================================
+template <class Op>
+__device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+                                              int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
+    const Vectors V = a.V;
+    double *x = a.x;
+    const bool fixed = a.fixed != 0;
+    const bool v3 = a.variant == 3;
+    // buffers: variant 3 ping-pongs p between V.p / V.z and s between V.s / V.w
+    double *pA = V.p, *pB = V.z, *sA = V.s, *sB = V.w;
+
+    // r_0 := b - A x_0; shadow r0 := r_0; p_0 := r_0 (as r + 0 (0 - 0 s))
+    double d0[1] = {0.0};
+    PBCG_ROWS(i) {
+        const double ri = a.b[i] - A.row(i, VecLoad{x});
+        V.r[i] = ri;
+        V.r0[i] = ri;
+        pA[i] = 0.0;
+        sA[i] = 0.0;
+        d0[0] = fma(ri, ri, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    double rho = d0[0];
+    o.nr0 = sqrt(rho);
+    o.nr = o.nr0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
+    const double tol = __dmul_rn(a.rtol, o.nr0);
+    if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
+    double beta = 0.0, omega = 0.0;
+
+    int it = 0;
+    while (it < a.limit) {
+        // ---- s_i = A p_i, alpha_i = (r0, r_i) / (r0, s_i)
+        double d1[1] = {0.0};
+        if (v3) {
+            const PLoad pl{V.r, pA, sA, beta, omega};
+            PBCG_ROWS(i) {
+                const double si = A.row(i, pl);
+                pB[i] = pl(i);
+                sB[i] = si;
+                d1[0] = fma(V.r0[i], si, d1[0]);
+            }
+        } else {
+            PBCG_ROWS(i) { pA[i] = fma(beta, fma(-omega, sA[i], pA[i]), V.r[i]); }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double si = A.row(i, VecLoad{pA});
+                sA[i] = si;
+                d1[0] = fma(V.r0[i], si, d1[0]);
+            }
+        }
+        ++spmvs;
+        double *pc = v3 ? pB : pA, *sc = v3 ? sB : sA;   // p_i, s_i
+        if (!grid_sum<1>(g, d1, sm, sflag)) return false;
+        if (!isfinite(d1[0])) { o.status = PBCG_NONFINITE; break; }
+        if (d1[0] == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        const double alpha = __ddiv_rn(rho, d1[0]);
+
+        // ---- q_i = r_i - alpha s_i; y_i = A q_i; omega_i
+        double d2[3] = {0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q)
+        if (v3) {
+            const QLoad ql{V.r, sc, alpha};
+            PBCG_ROWS(i) {
+                const double yi = A.row(i, ql);
+                const double qi = ql(i);
+                V.q[i] = qi;
+                V.y[i] = yi;
+                d2[0] = fma(qi, yi, d2[0]);
+                d2[1] = fma(yi, yi, d2[1]);
+                d2[2] = fma(qi, qi, d2[2]);
+            }
+        } else {
+            PBCG_ROWS(i) { V.q[i] = fma(-alpha, sc[i], V.r[i]); }
+            if (!grid_sync(g, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double yi = A.row(i, VecLoad{V.q});
+                const double qi = V.q[i];
+                V.y[i] = yi;
+                d2[0] = fma(qi, yi, d2[0]);
+                d2[1] = fma(yi, yi, d2[1]);
+                d2[2] = fma(qi, qi, d2[2]);
+            }
+        }
+        ++spmvs;
+        if (!grid_sum<3>(g, d2, sm, sflag)) return false;
+        const double qy = d2[0], yy = d2[1], qq = d2[2];
+        if (!all_finite(d2, 3)) { o.status = PBCG_NONFINITE; break; }
+        const double nq = sqrt(qq);
+        const bool small_q = !fixed && nq <= tol;
+        if (small_q || yy == 0.0) {
+            if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
+            PBCG_ROWS(i) { x[i] = fma(alpha, pc[i], x[i]); }
+            if (!grid_sync(g, sflag)) return false;
+            ++it;
+            o.nr = nq;
+            o.half = 1;
+            o.status = PBCG_OK;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = nq;
+            break;
+        }
+        omega = __ddiv_rn(qy, yy);
+        if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+
+        // ---- x_{i+1}, r_{i+1}; beta_i
+        double d3[2] = {0.0, 0.0};   // (r0,r) (r,r)
+        PBCG_ROWS(i) {
+            const double qi = V.q[i];
+            x[i] = fma(omega, qi, fma(alpha, pc[i], x[i]));
+            const double rn = fma(-omega, V.y[i], qi);
+            V.r[i] = rn;
+            d3[0] = fma(V.r0[i], rn, d3[0]);
+            d3[1] = fma(rn, rn, d3[1]);
+        }
+        if (!grid_sum<2>(g, d3, sm, sflag)) return false;
+        ++it;
+        const double rho_n = d3[0];
+        o.nr = sqrt(d3[1]);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = o.nr;
+        if (!all_finite(d3, 2)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && o.nr <= tol) { o.status = PBCG_OK; break; }
+        if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        beta = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_n, rho));
+        rho = rho_n;
+        if (v3) {
+            double *tp = pA; pA = pB; pB = tp;
+            double *ts = sA; sA = sB; sB = ts;
+        }
+    }
+    o.iters = it;
+    if (it == a.limit && o.status == PBCG_NOT_CONVERGED && fixed) o.status = PBCG_OK;
+    return true;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(kTPB) bicgstab_kernel(const Op A, const SolveArgs a) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ int sflag;
+    GridSync g{a.ctl, a.partials, 0u, 0};
+    const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
+    const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
+    Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+    int spmvs = 0;
+    if (!standard_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
+    finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+}
+
+// y = A x, one row per thread, grid-stride.
+template <class Op>
+__global__ void __launch_bounds__(kTPB) spmv_kernel(const Op A, const double *x, double *y) {
+    const VecLoad u{x};
+    for (int i = blockIdx.x * kTPB + threadIdx.x; i < A.n; i += gridDim.x * kTPB) y[i] = A.row(i, u);
+}
+
+// CSR structure check: rowptr[0] == 0, non-decreasing, rowptr[n] == nnz, 0 <= col < n.
+__global__ void csr_check_kernel(int n, int nnz, const int *rowptr, const int *col, int *bad) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        const int a = rowptr[i];
+        if (i == 0 && a != 0) atomicOr(bad, 1);
+        if (i == n && a != nnz) atomicOr(bad, 2);
+        if (i < n && rowptr[i + 1] < a) atomicOr(bad, 4);
+        if (a < 0 || a > nnz) atomicOr(bad, 8);
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) {
+        const int c = col[k];
+        if (c < 0 || c >= n) atomicOr(bad, 16);
+    }
+}
+
+#undef PBCG_ROWS
+
+}  // namespace pbcg

@@ -1,0 +1,305 @@
+"""Python binding of the C ABI in include/pbicgstab.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and takes raw
+pointers (Python ints) and sizes, exactly like the C ABI; ``Solver`` is a thin
+convenience layer that keeps device buffers in PyTorch tensors. All solver
+arithmetic runs in the CUDA library; if the library is not built this module
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_INCLUDE = os.path.join(_ROOT, "include")
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libpbicgstab.so")
+NVCC_ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+PBCG_OK, PBCG_NOT_CONVERGED, PBCG_BREAKDOWN, PBCG_NONFINITE = 0, 1, 2, 3
+PBCG_ERR_ARG, PBCG_ERR_CUDA, PBCG_ERR_OOM, PBCG_ERR_TIMEOUT = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: "ERR_ARG",
+                5: "ERR_CUDA", 6: "ERR_OOM", 7: "ERR_TIMEOUT"}
+PBCG_PREC_NONE, PBCG_PREC_JACOBI = 0, 1
+
+# Exported symbols, as declared in include/pbicgstab.h.
+EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_create_csr", "pbicgstab_create_stencil",
+           "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
+           "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error"]
+
+
+class PbcgCoef(ctypes.Structure):
+    _fields_ = [("value", ctypes.c_double), ("data", ctypes.c_void_p), ("stride", ctypes.c_int64 * 3),
+                ("len", ctypes.c_int64), ("data2", ctypes.c_void_p), ("stride2", ctypes.c_int64 * 3),
+                ("len2", ctypes.c_int64)]
+
+
+class PbcgStencil(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("coef", PbcgCoef * 7)]
+
+
+class PbcgOpts(ctypes.Structure):
+    _fields_ = [("max_replacements", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
+                ("d_history", ctypes.c_void_p), ("plain_variant", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
+class PbcgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("half_step", ctypes.c_int32),
+                ("n_replacements", ctypes.c_int32), ("nr0", ctypes.c_double),
+                ("rel_res_recursive", ctypes.c_double), ("rel_res_true", ctypes.c_double),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("grid_syncs", ctypes.c_int32),
+                ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def sources():
+    return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC)) if f.endswith((".cu", ".cuh"))] + \
+        [os.path.join(_INCLUDE, "pbicgstab.h")]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library for sm_103a with nvcc (in-tree, under _build/)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(LIB_PATH):
+        newest = max(os.path.getmtime(p) for p in sources())
+        if os.path.getmtime(LIB_PATH) >= newest:
+            return LIB_PATH
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["nvcc", NVCC_ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           "-I", _INCLUDE, "-o", tmp, os.path.join(_CSRC, "pbicgstab.cu")]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run paper_1612_01395_gb300.native.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, f64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+        L.pbicgstab_workspace_bytes.argtypes = [i32]
+        L.pbicgstab_workspace_bytes.restype = sz
+        L.pbicgstab_create_csr.argtypes = [i32, i32, vp, vp, vp, ctypes.c_int, vp, sz, vp, ctypes.POINTER(vp)]
+        L.pbicgstab_create_stencil.argtypes = [ctypes.POINTER(PbcgStencil), ctypes.c_int, vp, sz, vp,
+                                               ctypes.POINTER(vp)]
+        L.pbicgstab_solve.argtypes = [vp, vp, vp, f64, i32, i32, ctypes.POINTER(PbcgOpts), ctypes.POINTER(PbcgInfo)]
+        L.bicgstab_solve.argtypes = [vp, vp, vp, f64, i32, ctypes.POINTER(PbcgOpts), ctypes.POINTER(PbcgInfo)]
+        L.pbicgstab_solve_host.argtypes = [vp, i32, vp, vp, f64, i32, i32, ctypes.POINTER(PbcgOpts),
+                                           ctypes.POINTER(PbcgInfo)]
+        L.pbicgstab_spmv.argtypes = [vp, vp, vp]
+        L.pbicgstab_size.argtypes = [vp]
+        L.pbicgstab_size.restype = i32
+        L.pbicgstab_destroy.argtypes = [vp]
+        L.pbicgstab_destroy.restype = None
+        L.pbicgstab_last_error.argtypes = []
+        L.pbicgstab_last_error.restype = ctypes.c_char_p
+        for name in ("pbicgstab_create_csr", "pbicgstab_create_stencil", "pbicgstab_solve", "bicgstab_solve",
+                     "pbicgstab_solve_host", "pbicgstab_spmv"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class PbcgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _opts(max_replacements=-1, fixed_iters=0, d_history=None, plain_variant=0, grid=0):
+    return PbcgOpts(int(max_replacements), int(fixed_iters), d_history or None, int(plain_variant), int(grid))
+
+
+# ---- thin wrappers with the C names ---------------------------------------------------------
+
+def pbicgstab_workspace_bytes(n: int) -> int:
+    return int(lib().pbicgstab_workspace_bytes(int(n)))
+
+
+def pbicgstab_last_error() -> str:
+    return lib().pbicgstab_last_error().decode()
+
+
+def _check_create(st):
+    if st != PBCG_OK:
+        raise PbcgError(st, pbicgstab_last_error())
+
+
+def pbicgstab_create_csr(n, nnz, d_rowptr, d_col, d_val, prec, d_ws, ws_bytes, stream) -> int:
+    out = ctypes.c_void_p()
+    _check_create(lib().pbicgstab_create_csr(int(n), int(nnz), d_rowptr, d_col, d_val, int(prec), d_ws,
+                                             int(ws_bytes), stream, ctypes.byref(out)))
+    return out.value
+
+
+def pbicgstab_create_stencil(desc: PbcgStencil, prec, d_ws, ws_bytes, stream) -> int:
+    out = ctypes.c_void_p()
+    _check_create(lib().pbicgstab_create_stencil(ctypes.byref(desc), int(prec), d_ws, int(ws_bytes), stream,
+                                                 ctypes.byref(out)))
+    return out.value
+
+
+def pbicgstab_solve(h, d_b, d_x, rtol, maxit, replace_period=0, **opts):
+    info = PbcgInfo()
+    o = _opts(**opts)
+    st = lib().pbicgstab_solve(h, d_b, d_x, float(rtol), int(maxit), int(replace_period), ctypes.byref(o),
+                               ctypes.byref(info))
+    return st, info
+
+
+def bicgstab_solve(h, d_b, d_x, rtol, maxit, **opts):
+    info = PbcgInfo()
+    o = _opts(**opts)
+    st = lib().bicgstab_solve(h, d_b, d_x, float(rtol), int(maxit), ctypes.byref(o), ctypes.byref(info))
+    return st, info
+
+
+def pbicgstab_solve_host(h, method, h_b, h_x, rtol, maxit, replace_period=0, **opts):
+    info = PbcgInfo()
+    o = _opts(**opts)
+    st = lib().pbicgstab_solve_host(h, int(method), h_b, h_x, float(rtol), int(maxit), int(replace_period),
+                                    ctypes.byref(o), ctypes.byref(info))
+    return st, info
+
+
+def pbicgstab_spmv(h, d_x, d_y) -> int:
+    return lib().pbicgstab_spmv(h, d_x, d_y)
+
+
+def pbicgstab_size(h) -> int:
+    return lib().pbicgstab_size(h)
+
+
+def pbicgstab_destroy(h) -> None:
+    lib().pbicgstab_destroy(h)
+
+
+# ---- convenience layer over torch tensors ----------------------------------------------------
+
+class Solver:
+    """A handle plus the device buffers it refers to, kept alive in torch tensors.
+
+    ``Solver.from_csr(csr)`` / ``Solver.from_stencil(stencil)`` take the host
+    structures of ``problems`` (numpy arrays) and copy them to the device.
+    """
+
+    def __init__(self):
+        self.h = None
+        self._keep = []
+
+    @staticmethod
+    def _torch():
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        return torch
+
+    def _workspace(self, n, stream):
+        torch = self._torch()
+        nbytes = pbicgstab_workspace_bytes(n)
+        ws = torch.empty(nbytes // 8 + 64, dtype=torch.float64, device="cuda")
+        base = ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self._keep.append(ws)
+        self.ws_bytes = nbytes
+        self.n = n
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        return aligned, nbytes
+
+    @classmethod
+    def from_csr(cls, A, stream=None) -> "Solver":
+        self = cls()
+        torch = self._torch()
+        rowptr = torch.as_tensor(A.rowptr, dtype=torch.int32).cuda()
+        col = torch.as_tensor(A.col, dtype=torch.int32).cuda()
+        val = torch.as_tensor(A.val, dtype=torch.float64).cuda()
+        self._keep += [rowptr, col, val]
+        ws, nb = self._workspace(A.n, stream)
+        self.h = pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), col.data_ptr() if A.nnz else None,
+                                      val.data_ptr() if A.nnz else None, PBCG_PREC_NONE, ws, nb,
+                                      self.stream.cuda_stream)
+        return self
+
+    @classmethod
+    def from_stencil(cls, st, stream=None) -> "Solver":
+        self = cls()
+        torch = self._torch()
+        desc = PbcgStencil()
+        desc.nx, desc.ny, desc.nz = st.nx, st.ny, st.nz
+        for d, c in enumerate(st.coefs):
+            cd = desc.coef[d]
+            cd.value = float(c.value)
+            if c.table is not None:
+                t = torch.as_tensor(c.table, dtype=torch.float64).cuda()
+                self._keep.append(t)
+                cd.data = t.data_ptr()
+                cd.len = t.numel()
+                cd.stride[:] = [int(v) for v in c.stride]
+            if c.table2 is not None:
+                t2 = torch.as_tensor(c.table2, dtype=torch.float64).cuda()
+                self._keep.append(t2)
+                cd.data2 = t2.data_ptr()
+                cd.len2 = t2.numel()
+                cd.stride2[:] = [int(v) for v in c.stride2]
+        ws, nb = self._workspace(st.n, stream)
+        self.h = pbicgstab_create_stencil(desc, PBCG_PREC_NONE, ws, nb, self.stream.cuda_stream)
+        return self
+
+    def spmv(self, x):
+        torch = self._torch()
+        y = torch.empty_like(x)
+        st = pbicgstab_spmv(self.h, x.data_ptr(), y.data_ptr())
+        if st != PBCG_OK:
+            raise PbcgError(st, pbicgstab_last_error())
+        return y
+
+    def solve(self, b, x0=None, rtol=1e-8, maxit=1000, replace_period=0, method="pipelined",
+              history=False, **opts):
+        """Solve A x = b on the device; returns (x, info dict[, history tensor])."""
+        torch = self._torch()
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        hist = None
+        if history:
+            steps = opts.get("fixed_iters", 0) or maxit
+            hist = torch.full((steps + 1,), float("nan"), dtype=torch.float64, device=b.device)
+            opts["d_history"] = hist.data_ptr()
+        if method == "pipelined":
+            st, info = pbicgstab_solve(self.h, b.data_ptr(), x.data_ptr(), rtol, maxit, replace_period, **opts)
+        elif method == "standard":
+            st, info = bicgstab_solve(self.h, b.data_ptr(), x.data_ptr(), rtol, maxit, **opts)
+        else:
+            raise ValueError(method)
+        if st in (PBCG_ERR_ARG, PBCG_ERR_CUDA, PBCG_ERR_OOM, PBCG_ERR_TIMEOUT):
+            raise PbcgError(st, pbicgstab_last_error())
+        d = info.as_dict()
+        if hist is not None:
+            return x, d, hist[: d["iters"] + 1]
+        return x, d
+
+    def close(self):
+        if self.h:
+            pbicgstab_destroy(self.h)
+            self.h = None
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,255 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI (needs a GB300).
+
+Floating-point bar (from the acceptance criteria of the pipelined solver): after
+the oracle's iteration count, ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-9, and
+the recursive residual norms of the first 20 iterations agree to 1e-8
+relative. The two sides round differently (the GPU fuses multiply-adds and sums
+dot products in a tree), so results are not bitwise equal; SpMV rows are
+compared to 1e-14.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01395_gb300 import native, problems as P
+
+pytestmark = pytest.mark.gpu
+
+X_TOL = 1e-9
+HIST_TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    native.build()
+    native.lib()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def problem(name):
+    if name == "cd2d_64":
+        st = P.cd2d_constant(64, (10.0, 10.0))
+    elif name == "cd2d_37":
+        st = P.cd2d_constant(37, (10.0, 4.0))
+    elif name == "cd3d_13":
+        st = P.cd3d_trig(13)
+    elif name == "cd3d_20":
+        st = P.cd3d_trig(20)
+    elif name == "ptp1_40":
+        st = P.ptp1(40)
+    elif name == "rand_3001":
+        return None, P.random_sparse(3001, seed=5)
+    else:
+        raise KeyError(name)
+    return st, P.stencil_to_csr(st)
+
+
+def solver_for(name, form):
+    st, A = problem(name)
+    if form == "stencil":
+        if st is None:
+            pytest.skip("no stencil form")
+        return native.Solver.from_stencil(st), A
+    return native.Solver.from_csr(A), A
+
+
+NAMES = ["cd2d_64", "cd2d_37", "cd3d_13", "cd3d_20", "ptp1_40", "rand_3001"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("form", ["csr", "stencil"])
+def test_spmv_matches_oracle(name, form):
+    s, A = solver_for(name, form)
+    x = P.splitmix64_uniform(17, A.n)
+    y = host(s.spmv(dev(x)))
+    ref = oracle.spmv(A, x)
+    np.testing.assert_allclose(y, ref, rtol=1e-14, atol=1e-14 * np.max(np.abs(ref)))
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["cd2d_37", "cd3d_13", "ptp1_40"])
+def test_stencil_and_csr_products_identical(name):
+    st, A = problem(name)
+    s1, s2 = native.Solver.from_stencil(st), native.Solver.from_csr(A)
+    x = dev(P.splitmix64_uniform(3, A.n))
+    np.testing.assert_array_equal(host(s1.spmv(x)), host(s2.spmv(x)))
+
+
+def oracle_run(method, A, b, **kw):
+    fn = {"pipelined": oracle.pbicgstab, "standard": oracle.bicgstab}[method]
+    return fn(A, b, **kw)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("form", ["csr", "stencil"])
+@pytest.mark.parametrize("method,variant", [("pipelined", 0), ("standard", 3), ("standard", 5)])
+def test_fixed_iterations_match_oracle(name, form, method, variant):
+    s, A = solver_for(name, form)
+    xs = P.splitmix64_uniform(0, A.n)
+    b = oracle.spmv(A, xs)
+    ref = oracle_run(method, A, b, rtol=1e-8, maxit=2000)
+    assert ref.status == oracle.CONVERGED
+    k = ref.iters - (1 if ref.half_step else 0)
+    fx = oracle_run(method, A, b, rtol=0.0, maxit=k, fixed_iters=k)
+    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=k, fixed_iters=k, history=True, method=method,
+                            plain_variant=variant)
+    assert info["status"] == native.PBCG_OK and info["iters"] == k
+    assert rel(host(x), fx.x) <= X_TOL
+    h, hr = host(hist)[:21], fx.hist[:21]
+    assert np.max(np.abs(h - hr) / hr) <= HIST_TOL
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["cd2d_64", "cd3d_20", "rand_3001"])
+@pytest.mark.parametrize("method", ["pipelined", "standard"])
+def test_free_run_converges_like_oracle(name, method):
+    s, A = solver_for(name, "csr")
+    xs = P.splitmix64_uniform(0, A.n)
+    b = oracle.spmv(A, xs)
+    ref = oracle_run(method, A, b, rtol=1e-8, maxit=2000)
+    x, info = s.solve(dev(b), rtol=1e-8, maxit=2000, method=method)
+    assert info["status"] == native.PBCG_OK
+    assert abs(info["iters"] - ref.iters) <= max(3, 0.05 * ref.iters)
+    # the true residual of the returned x, recomputed by the oracle
+    true_rel = np.linalg.norm(b - oracle.spmv(A, host(x))) / ref.nr0
+    assert true_rel <= 1e-8
+    assert abs(info["rel_res_true"] - true_rel) <= 1e-3 * true_rel + 1e-15
+    s.close()
+
+
+@pytest.mark.parametrize("k", [5, 10, 20])
+def test_residual_replacement_matches_oracle(k):
+    s, A = solver_for("cd2d_64", "stencil")
+    xs = P.splitmix64_uniform(0, A.n)
+    b = oracle.spmv(A, xs)
+    ref = oracle.pbicgstab(A, b, rtol=1e-12, maxit=600, replace_period=k)
+    assert ref.status == oracle.CONVERGED
+    steps = ref.iters - (1 if ref.half_step else 0)
+    fx = oracle.pbicgstab(A, b, rtol=0.0, maxit=steps, fixed_iters=steps, replace_period=k)
+    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=steps, fixed_iters=steps, replace_period=k, history=True)
+    assert info["n_replacements"] == fx.n_replacements == steps // k
+    assert rel(host(x), fx.x) <= X_TOL
+    assert np.max(np.abs(host(hist)[:21] - fx.hist[:21]) / fx.hist[:21]) <= HIST_TOL
+    s.close()
+
+
+def test_replacement_restores_accuracy_on_gpu():
+    s, A = solver_for("cd2d_64", "stencil")
+    b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
+    bd = dev(b)
+    _, plain = s.solve(bd, rtol=1e-14, maxit=600, method="standard")
+    _, pipe = s.solve(bd, rtol=1e-14, maxit=600)
+    _, rr = s.solve(bd, rtol=1e-14, maxit=600, replace_period=20)
+    assert pipe["rel_res_true"] > 100 * plain["rel_res_true"]
+    assert rr["status"] == native.PBCG_OK and rr["rel_res_true"] < 1e-13
+    _, capped = s.solve(bd, rtol=1e-14, maxit=600, replace_period=10, max_replacements=3)
+    assert capped["n_replacements"] == 3
+
+
+def test_deterministic_and_grid_independent():
+    s, A = solver_for("cd3d_20", "stencil")
+    b = oracle.spmv(A, P.splitmix64_uniform(1, A.n))
+    ref = oracle.pbicgstab(A, b, rtol=0.0, maxit=40, fixed_iters=40)
+    bd = dev(b)
+    x1, i1 = s.solve(bd, rtol=0.0, maxit=40, fixed_iters=40)
+    x2, i2 = s.solve(bd, rtol=0.0, maxit=40, fixed_iters=40)
+    np.testing.assert_array_equal(host(x1), host(x2))
+    for g in (1, 3, 64, 250):
+        xg, ig = s.solve(bd, rtol=0.0, maxit=40, fixed_iters=40, grid=g)
+        assert ig["grid"] == g
+        assert rel(host(xg), ref.x) <= X_TOL
+
+
+def test_initial_guess_and_host_entry_point():
+    import torch
+    s, A = solver_for("cd2d_37", "csr")
+    xs = P.splitmix64_uniform(0, A.n)
+    b = oracle.spmv(A, xs)
+    x0 = xs + 1e-3 * P.splitmix64_uniform(9, A.n)
+    ref = oracle.pbicgstab(A, b, x0=x0, rtol=0.0, maxit=15, fixed_iters=15)
+    x, info = s.solve(dev(b), x0=dev(x0), rtol=0.0, maxit=15, fixed_iters=15)
+    assert rel(host(x), ref.x) <= X_TOL
+    hb = torch.from_numpy(b.copy()).pin_memory()
+    hx = torch.from_numpy(x0.copy()).pin_memory()
+    st, inf = native.pbicgstab_solve_host(s.h, 0, hb.data_ptr(), hx.data_ptr(), 0.0, 15, 0, fixed_iters=15)
+    assert st == native.PBCG_OK
+    np.testing.assert_array_equal(hx.numpy(), host(x))
+
+
+def test_small_and_degenerate_systems():
+    # n = 1: one half step gives the exact solution
+    A1 = P.dense_to_csr(np.array([[3.0]]))
+    s = native.Solver.from_csr(A1)
+    x, info = s.solve(dev(np.array([6.0])), rtol=1e-12, maxit=10)
+    assert info["status"] == native.PBCG_OK and info["half_step"] == 1 and host(x)[0] == 2.0
+    # A = 2I: half step, x = b / 2 exactly
+    n = 1000
+    s = native.Solver.from_csr(P.dense_to_csr(2.0 * np.eye(n)) if n <= 1000 else None)
+    b = P.splitmix64_uniform(5, n)
+    x, info = s.solve(dev(b), rtol=1e-10, maxit=10)
+    assert info["iters"] == 1 and info["half_step"] == 1
+    np.testing.assert_array_equal(host(x), b / 2.0)
+    # zero right-hand side: nothing to do
+    x, info = s.solve(dev(np.zeros(n)), rtol=1e-10, maxit=10)
+    assert info["status"] == native.PBCG_OK and info["iters"] == 0 and not host(x).any()
+    # maxit = 0
+    st, A = problem("cd2d_37")
+    s = native.Solver.from_csr(A)
+    x, info = s.solve(dev(np.ones(A.n)), rtol=1e-10, maxit=0)
+    assert info["status"] == native.PBCG_NOT_CONVERGED and info["iters"] == 0
+
+
+@pytest.mark.parametrize("method", ["pipelined", "standard"])
+def test_breakdown_and_nonfinite(method):
+    A = P.dense_to_csr(np.array([[0.0, 1.0], [1.0, 0.0]]))
+    s = native.Solver.from_csr(A)
+    x, info = s.solve(dev(np.array([1.0, 0.0])), rtol=1e-10, maxit=10, method=method)
+    assert info["status"] == native.PBCG_BREAKDOWN and info["iters"] == 0
+    assert not host(x).any()
+    st, A = problem("cd2d_37")
+    s = native.Solver.from_csr(A)
+    b = np.ones(A.n)
+    b[11] = np.nan
+    x, info = s.solve(dev(b), rtol=1e-10, maxit=10, method=method)
+    assert info["status"] == native.PBCG_NONFINITE
+
+
+def test_create_rejects_bad_input():
+    import torch
+    A = P.stencil_to_csr(P.cd2d_constant(8))
+    rowptr = dev(A.rowptr)
+    col = A.col.copy()
+    col[5] = A.n          # out of range
+    cold, val = dev(col), dev(A.val)
+    nb = native.pbicgstab_workspace_bytes(A.n)
+    ws = torch.empty(nb // 8 + 64, dtype=torch.float64, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(native.PbcgError) as e:
+        native.pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), cold.data_ptr(), val.data_ptr(), 0, base, nb, stream)
+    assert e.value.status == native.PBCG_ERR_ARG
+    good = dev(A.col)
+    with pytest.raises(native.PbcgError) as e:
+        native.pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), good.data_ptr(), val.data_ptr(), 0, base, nb - 8,
+                                    stream)
+    assert e.value.status == native.PBCG_ERR_OOM
+    h = native.pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), good.data_ptr(), val.data_ptr(), 0, base, nb,
+                                    stream)
+    x = dev(np.ones(A.n))
+    assert native.pbicgstab_spmv(h, x.data_ptr(), x.data_ptr() + 8) == native.PBCG_ERR_ARG
+    native.pbicgstab_destroy(h)

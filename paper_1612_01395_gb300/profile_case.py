@@ -1,0 +1,62 @@
+"""One solver launch on a chosen problem, for profilers (ncu) and quick timing.
+
+Runs `--repeat` solves of a fixed number of iterations after one warm-up solve,
+so a profiler can skip the warm-up launch and capture the next one:
+
+    python -m paper_1612_01395_gb300.profile_case --problem cd3d --n 128 --iters 5 \\
+        --method pipelined --form stencil
+
+Problems: cd3d (3-D convection-diffusion, velocity (20 sin y, 20 cos z, 20 sin x),
+n^3 grid), cd2d (2-D, constant velocity (10, 10), n^2 grid).
+"""
+import argparse
+import json
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--problem", default="cd3d", choices=["cd3d", "cd2d"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--iters", type=int, default=5, help="fixed iterations per solve (0: solve to --rtol)")
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--method", default="pipelined", choices=["pipelined", "standard"])
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--form", default="stencil", choices=["stencil", "csr"])
+    ap.add_argument("--replace-period", type=int, default=0)
+    ap.add_argument("--grid", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    args = ap.parse_args(argv)
+
+    import torch
+    from paper_1612_01395_gb300 import native, problems as P
+    native.build()
+    st = P.cd3d_trig(args.n) if args.problem == "cd3d" else P.cd2d_constant(args.n, (10.0, 10.0))
+    s = native.Solver.from_stencil(st) if args.form == "stencil" else native.Solver.from_csr(P.stencil_to_csr(st))
+    xs = torch.from_numpy(P.splitmix64_uniform(0, st.n)).cuda()
+    b = s.spmv(xs)
+    kw = dict(method=args.method, plain_variant=args.variant, grid=args.grid, replace_period=args.replace_period)
+    if args.iters > 0:
+        kw.update(rtol=0.0, maxit=args.iters, fixed_iters=args.iters)
+    else:
+        kw.update(rtol=args.rtol, maxit=100000)
+    s.solve(b, **kw)                       # warm-up launch
+    out = []
+    for _ in range(args.repeat):
+        x, info = s.solve(b, **kw)
+        out.append(info)
+    torch.cuda.synchronize()
+    ms = [i["kernel_ms"] for i in out]
+    its = out[0]["iters"]
+    print(json.dumps({"problem": args.problem, "n": st.n, "form": args.form, "method": args.method,
+                      "iters": its, "kernel_ms": float(np.median(ms)),
+                      "us_per_iter": 1e3 * float(np.median(ms)) / max(its, 1), "grid": out[0]["grid"],
+                      "grid_syncs": out[0]["grid_syncs"], "status": out[0]["status"]}))
+    s.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

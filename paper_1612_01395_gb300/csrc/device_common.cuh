@@ -26,7 +26,7 @@ struct Control {
 };
 static_assert(sizeof(Control) <= 256, "control block must fit 256 bytes");
 constexpr size_t kControlBytes = 256;
-constexpr size_t kPartialBytes = 2ull * kMaxGrid * kMaxDots * sizeof(double);
+constexpr size_t kPartialBytes = 3ull * kMaxGrid * 8 * sizeof(double);   // 3 rotating slot buffers
 
 // n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply-high: the
 // round-up method of Granlund & Montgomery, "Division by invariant integers
@@ -59,94 +59,185 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
     return v;
 }
 
-// Butterfly sum over a warp. Every lane ends with the same bits: at each level
-// a lane adds its partner's value to its own, and addition is commutative.
+constexpr unsigned kFull = 0xffffffffu;
+
+// Sum of each of K values over the 32 lanes of a warp, returned to every lane.
+// FP64 adds are the scarce resource on this GPU (one warp-wide DADD occupies a
+// sub-partition's FP64 pipe for ~64 cycles), so the first log2(P) levels use
+// recursive halving (P = K rounded up to a power of two): at each level a lane
+// keeps half of its values and adds its partner's copy of them, costing P/2
+// additions instead of P; the remaining levels are a butterfly on one value.
+// K = 5 takes 9 additions instead of 25. After the halving, value index k
+// lives in the lanes whose bits 4, 3, 2 (most significant first) spell k.
+// Deterministic: in the butterfly both partners add the same two numbers (in
+// either order, hence to the same bits), so all lanes holding index k agree.
 template <int K>
-__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+__device__ __forceinline__ void warp_allsum(double (&v)[K]) {
+    constexpr int P = K <= 1 ? 1 : K <= 2 ? 2 : K <= 4 ? 4 : 8;
+    constexpr int M = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3;
+    static_assert(K <= 8, "at most 8 values");
+    const int lane = threadIdx.x & 31;
+    double w[P];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int k = 0; k < P; ++k) w[k] = k < K ? v[k] : 0.0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    for (int lvl = 0; lvl < M; ++lvl) {
+        const int o = 16 >> lvl;
+        const int half = P >> (lvl + 1);
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const double send = upper ? w[k] : w[k + half];
+            const double keep = upper ? w[k + half] : w[k];
+            w[k] = keep + __shfl_xor_sync(kFull, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> M; o > 0; o >>= 1) w[0] += __shfl_xor_sync(kFull, w[0], o);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int src = 0;
+#pragma unroll
+        for (int b = 0; b < M; ++b)
+            if (k & (1 << (M - 1 - b))) src |= 16 >> b;
+        v[k] = __shfl_sync(kFull, w[0], src);
     }
 }
 
-// Fixed-order block sum; every thread receives the result. sm: [kMaxDots][32].
+// Fixed-order block sum; every thread receives the K results. sm: [kMaxDots][32].
+// Warps reduce independently, then lane k of every warp adds value k of the
+// warps in warp order and shuffles it to the other lanes.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double (*sm)[32]) {
     constexpr int kWarps = kTPB / 32;
-    warp_sum<K>(v);
+    warp_allsum<K>(v);
+    if (kWarps == 1) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) sm[k][wid] = v[k];
     }
     __syncthreads();
+    double t = 0.0;
+    if (lane < K) {
+        t = sm[lane][0];
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = lane < kWarps ? sm[k][lane] : 0.0;
-    warp_sum<K>(v);   // each warp reduces the same kWarps values
+        for (int w = 1; w < kWarps; ++w) t += sm[lane][w];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = __shfl_sync(kFull, t, k);
     __syncthreads();
 }
 
-// Grid-wide synchronisation of a cooperative launch, optionally carrying a
-// fixed-order sum of K doubles. Arrivals are counted on one word; every wait is
-// bounded by kSyncTimeoutNs and by the abort flag, so a launch can only end.
+// Grid-wide exchange of a cooperative launch. Each block owns one 64-byte
+// slot (8 doubles) in each of 3 rotating buffers; exchange number e uses
+// buffer e % 3. A block publishes by (1) resetting its slot of buffer
+// (e+1) % 3 to the sentinel, (2) a gpu-scope fence, which orders every store
+// of the phase (made visible to thread 0 by __syncthreads) before (3) the
+// relaxed stores of its K partial sums into its slot of buffer e % 3. The
+// partial sums are the arrival signal: a reader polls each slot until none of
+// its K words is the sentinel, then fences (acquire) -- so one round trip
+// delivers both "everyone has arrived" and the data. The reset in (1) is safe:
+// buffer (e+1) % 3 last held exchange e-2, which every block has finished
+// reading before it published exchange e-1, which this block has seen.
+// Every wait is bounded (kSyncTimeoutNs) and watches the abort flag.
+// The host fills all slots with the sentinel before each launch.
+constexpr unsigned long long kSentinel = 0xFFFFFFFFFFFFFFFFull;   // a NaN that arithmetic never produces
+constexpr unsigned long long kQuietNaN = 0x7FF8000000000000ull;
+constexpr int kSlotDoubles = 8;
+
 struct GridSync {
     Control *ctl;
-    double *partials;   // [2][kMaxGrid][kMaxDots]
-    unsigned epoch;     // synchronisations passed by this block
-    int count;          // synchronisations performed (for diagnostics)
+    double *slots;      // [3][gridDim.x][kSlotDoubles]
+    unsigned epoch;     // exchanges done by this block
+    int count;          // exchanges performed (for diagnostics)
 };
 
-__device__ __forceinline__ bool grid_wait(GridSync &g, int *sflag) {
-    __syncthreads();   // every thread's stores of this phase precede the fence below
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&g.ctl->arrivals, 1u);
-        const unsigned target = (g.epoch + 1u) * gridDim.x;
-        const uint64_t t0 = globaltimer_ns();
-        int ok = 1;
-        while (ld_acquire_u32(&g.ctl->arrivals) < target) {
-            if (ld_relaxed_s32(&g.ctl->abort) != 0) { ok = 0; break; }
-            if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
-                atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        __threadfence();
-        *sflag = ok;
-    }
-    __syncthreads();
-    const bool ok = *sflag != 0;
-    g.epoch++;
-    g.count++;
-    return ok;
+__device__ __forceinline__ void st_relaxed_u64(double *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Barrier without data.
-__device__ __forceinline__ bool grid_sync(GridSync &g, int *sflag) { return grid_wait(g, sflag); }
+__device__ __forceinline__ double *slot_ptr(const GridSync &g, unsigned buf, int block) {
+    return g.slots + ((size_t)buf * gridDim.x + block) * kSlotDoubles;
+}
+
+// Publish the K values of this block (thread 0 only) and wait for all blocks;
+// acc receives, per thread, the fixed-order sum of slots tid, tid+kTPB, ...
+template <int K>
+__device__ __forceinline__ bool exchange(GridSync &g, const double (&mine)[K], double (&acc)[K], int *sflag) {
+    const unsigned buf = g.epoch % 3u, next = (g.epoch + 1u) % 3u;
+    if (threadIdx.x == 0) {
+        double *reset = slot_ptr(g, next, blockIdx.x);
+#pragma unroll
+        for (int k = 0; k < kSlotDoubles; ++k) reset[k] = __longlong_as_double((long long)kSentinel);
+        __threadfence();
+        double *out = slot_ptr(g, buf, blockIdx.x);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            unsigned long long bits = (unsigned long long)__double_as_longlong(mine[k]);
+            st_relaxed_u64(out + k, bits == kSentinel ? kQuietNaN : bits);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    bool ok = true;
+    const uint64_t t0 = globaltimer_ns();
+    for (int b = threadIdx.x; b < (int)gridDim.x && ok; b += kTPB) {
+        const double *src = slot_ptr(g, buf, b);
+        unsigned long long w[K];
+        unsigned spins = 0;
+        for (;;) {
+            bool ready = true;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                w[k] = ld_relaxed_u64(src + k);
+                ready = ready && w[k] != kSentinel;
+            }
+            if (ready) break;
+            if ((++spins & 63u) == 0) {
+                if (ld_relaxed_s32(&g.ctl->abort) != 0) { ok = false; break; }
+                if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
+                    atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __longlong_as_double((long long)w[k]);
+    }
+    __threadfence();   // acquire: later loads of this thread see what the publishers stored
+    if (!ok) *sflag = 0;
+    __syncthreads();
+    const bool all_ok = *sflag != 0;
+    g.epoch++;
+    g.count++;
+    return all_ok;
+}
+
+// Barrier without data (a dummy value is exchanged).
+__device__ __forceinline__ bool grid_sync(GridSync &g, double (*sm)[32], int *sflag) {
+    if (threadIdx.x == 0) *sflag = 1;
+    __syncthreads();   // every thread's stores of this phase precede thread 0's fence
+    const double one[1] = {1.0};
+    double acc[1];
+    return exchange<1>(g, one, acc, sflag);
+}
 
 // Barrier that also returns, in every thread of every block, the same
 // fixed-order sum over the grid of the K per-thread values v.
 template <int K>
 __device__ __forceinline__ bool grid_sum(GridSync &g, double (&v)[K], double (*sm)[32], int *sflag) {
-    block_sum<K>(v, sm);
-    const unsigned slot = g.epoch & 1u;
-    double *base = g.partials + (size_t)slot * kMaxGrid * kMaxDots;
-    if (threadIdx.x == 0) {
-        double *mine = base + (size_t)blockIdx.x * kMaxDots;
-#pragma unroll
-        for (int k = 0; k < K; ++k) mine[k] = v[k];
-    }
-    if (!grid_wait(g, sflag)) return false;
+    if (threadIdx.x == 0) *sflag = 1;
+    block_sum<K>(v, sm);   // ends with __syncthreads
     double acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kTPB) {
-        const double *src = base + (size_t)b * kMaxDots;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __ldcg(src + k);
-    }
+    if (!exchange<K>(g, v, acc, sflag)) return false;
     block_sum<K>(acc, sm);
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = acc[k];

@@ -49,12 +49,12 @@ struct CsrOp {
     }
 };
 
+// One coefficient: t1[i*a1 + j*b1 + k*c1] (or `value` when t1 is null) plus
+// t2[i*a2 + j*b2 + k*c2] when t2 is set. Indices fit 31 bits (checked at create).
 struct StCoef {
+    const double *t1, *t2;
+    int a1, b1, c1, a2, b2, c2;
     double value;
-    const double *t1;
-    long long a1, b1, c1;
-    const double *t2;
-    long long a2, b2, c2;
 };
 
 struct StencilOp {

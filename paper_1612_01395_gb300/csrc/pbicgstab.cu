@@ -157,6 +157,8 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
 
     const int grid = pick_grid(h, pipelined ? h->occ_pipe : h->occ_plain, o.grid);
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
+    // every exchange slot starts as the sentinel (all bits set)
+    PBCG_CUDA(cudaMemsetAsync(h->partials, 0xFF, 3ull * grid * pbcg::kSlotDoubles * sizeof(double), h->stream));
     PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
     if (h->n > 0) {
         pbcg_status st = h->kind == 0 ? launch_solver(h, h->csr, pipelined, a, grid)
@@ -257,6 +259,9 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
             return fail(PBCG_ERR_ARG, "coefficient %d: table too short (len %lld)", d, (long long)c.len);
         if (c.data2 && max_index(c.stride2, nx, ny, nz) >= c.len2)
             return fail(PBCG_ERR_ARG, "coefficient %d: second table too short (len %lld)", d, (long long)c.len2);
+        if ((c.data && max_index(c.stride, nx, ny, nz) >= (1ll << 31)) ||
+            (c.data2 && max_index(c.stride2, nx, ny, nz) >= (1ll << 31)))
+            return fail(PBCG_ERR_ARG, "coefficient %d: table index exceeds 2^31-1", d);
     }
     pbicgstab_s *h = new (std::nothrow) pbicgstab_s();
     if (!h) return fail(PBCG_ERR_OOM, "host allocation failed");
@@ -273,8 +278,17 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
         o.dy.init((uint32_t)ny);
         for (int d = 0; d < 7; ++d) {
             const pbcg_coef &c = desc->coef[d];
-            o.c[d] = pbcg::StCoef{c.value, c.data, c.stride[0], c.stride[1], c.stride[2],
-                                  c.data2, c.stride2[0], c.stride2[1], c.stride2[2]};
+            pbcg::StCoef q;
+            q.t1 = c.data;
+            q.t2 = c.data2;
+            q.a1 = c.data ? (int)c.stride[0] : 0;
+            q.b1 = c.data ? (int)c.stride[1] : 0;
+            q.c1 = c.data ? (int)c.stride[2] : 0;
+            q.a2 = c.data2 ? (int)c.stride2[0] : 0;
+            q.b2 = c.data2 ? (int)c.stride2[1] : 0;
+            q.c2 = c.data2 ? (int)c.stride2[2] : 0;
+            q.value = c.value;
+            o.c[d] = q;
         }
         st = occupancy<pbcg::StencilOp>(&h->occ_pipe, &h->occ_plain);
     }

@@ -41,20 +41,57 @@ struct SolveArgs {
     int variant;        // Algorithm 7 only: 3 or 5
 };
 
-struct Outcome {
-    int iters, status, half, nrr;
-    double nr0, nr;
+// Resident blocks per SM the solver kernels are compiled for (register cap
+// 65536 / (kTPB * kMinBlocks)): the large-n sweeps are limited by the FP64 pipe,
+// which needs many warps in flight to cover memory latency. The stencil's
+// coefficient evaluation needs a little more registers than CSR.
+template <class Op>
+struct Tune {
+    static constexpr int kMinBlocks = 8;
+};
+template <>
+struct Tune<StencilOp> {
+    static constexpr int kMinBlocks = 6;
 };
 
-__device__ __forceinline__ bool all_finite(const double *v, int k) {
-    for (int i = 0; i < k; ++i)
-        if (!isfinite(v[i])) return false;
-    return true;
+struct Outcome {
+    int iters, status, half, nrr;
+    double nr0, nr;   // nr: squared norm of the last recursive residual (or of q after a half step)
+};
+
+template <int K>
+__device__ __forceinline__ bool all_finite(const double (&v)[K]) {
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < K; ++i) ok = ok && isfinite(v[i]);
+    return ok;
 }
 
 #define PBCG_ROWS(i) for (int i = lo + (int)threadIdx.x; i < hi; i += kTPB)
 
-// Final true residual ||b - A x|| and the result record (block 0).
+// Stopping tests compare squared norms first, so that the square root (about
+// ten FP64 instructions, ~700 cycles per warp on this GPU) stays off the
+// critical path: sqrt(a) <= tol implies a <= 2 tol^2, and the exact test
+// sqrt(a) <= tol is then evaluated only in that rare case.
+__device__ __forceinline__ bool norm_below(double sq, double tol, double tol2) {
+    return (sq <= 2.0 * tol2 || !(tol2 >= 2.2250738585072014e-308)) && sqrt(sq) <= tol;
+}
+
+// beta = (alpha / omega) (rho_n / rho): the two divisions are independent, so
+// warps 0 and 1 evaluate one each (every warp has its own FP64 pipe) and share
+// them through shared memory.
+__device__ __forceinline__ double beta_of(double alpha, double omega, double rho_n, double rho, double *sq) {
+    const int wid = threadIdx.x >> 5;
+    if (wid == 0) sq[0] = __ddiv_rn(alpha, omega);
+    if (wid == 1) sq[1] = __ddiv_rn(rho_n, rho);
+    __syncthreads();
+    const double b = __dmul_rn(sq[0], sq[1]);
+    __syncthreads();
+    return b;
+}
+
+// Final true residual ||b - A x|| and the result record (block 0). The
+// history holds squared norms during the loop; they become norms here.
 template <class Op>
 __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32], int *sflag,
                                        int lo, int hi, const Outcome &o, int spmvs) {
@@ -64,18 +101,23 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
         d[0] = fma(res, res, d[0]);
     }
     if (!grid_sum<1>(g, d, sm, sflag)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Control *c = a.ctl;
-        const double nt = sqrt(d[0]);
-        c->iters = o.iters;
-        c->status = o.status;
-        c->half_step = o.half;
-        c->n_repl = o.nrr;
-        c->grid_syncs = g.count;
-        c->spmvs = spmvs + 1;
-        c->nr0 = o.nr0;
-        c->rel_rec = o.nr0 > 0.0 ? o.nr / o.nr0 : 0.0;
-        c->rel_true = o.nr0 > 0.0 ? nt / o.nr0 : nt;
+    if (blockIdx.x == 0) {
+        if (a.hist)
+            for (int i = 1 + (int)threadIdx.x; i <= o.iters; i += kTPB) a.hist[i] = sqrt(a.hist[i]);
+        if (threadIdx.x == 0) {
+            Control *c = a.ctl;
+            const double nt = sqrt(d[0]);
+            const double nr = o.iters > 0 ? sqrt(o.nr) : o.nr0;
+            c->iters = o.iters;
+            c->status = o.status;
+            c->half_step = o.half;
+            c->n_repl = o.nrr;
+            c->grid_syncs = g.count;
+            c->spmvs = spmvs + 1;
+            c->nr0 = o.nr0;
+            c->rel_rec = o.nr0 > 0.0 ? nr / o.nr0 : 0.0;
+            c->rel_true = o.nr0 > 0.0 ? nt / o.nr0 : nt;
+        }
     }
 }
 
@@ -87,7 +129,7 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
 template <class Op>
 __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
                                                int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
-    const Vectors V = a.V;
+    const Vectors &V = a.V;
     double *x = a.x;
     const bool fixed = a.fixed != 0;
 
@@ -109,7 +151,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
     o.nr0 = sqrt(rho);
     o.nr = o.nr0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
-    const double tol = __dmul_rn(a.rtol, o.nr0);
+    const double tol = __dmul_rn(a.rtol, o.nr0), tol2 = __dmul_rn(tol, tol);
     if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
 
     // w_0 := A r_0; alpha_0 := (r0, r0) / (r0, w0)
@@ -159,9 +201,9 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
                 V.t[i] = A.row(i, VecLoad{V.w});
                 V.p[i] = fma(beta, fma(-omega, V.s[i], V.p[i]), V.r[i]);
             }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) { V.s[i] = A.row(i, VecLoad{V.p}); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const double zn = A.row(i, VecLoad{V.s});
                 const double sn = V.s[i], ri = V.r[i], wi = V.w[i];
@@ -181,18 +223,17 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
         }
         if (!grid_sum<5>(g, d1, sm, sflag)) return false;
         const double qy = d1[0], yy = d1[1], qq = d1[2], r0s = d1[3], r0z = d1[4];
-        if (!all_finite(d1, 5)) { o.status = PBCG_NONFINITE; break; }
-        const double nq = sqrt(qq);
-        const bool small_q = !fixed && nq <= tol;
+        if (!all_finite(d1)) { o.status = PBCG_NONFINITE; break; }
+        const bool small_q = !fixed && norm_below(qq, tol, tol2);
         if (small_q || yy == 0.0) {
             if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
             PBCG_ROWS(i) { x[i] = fma(alpha, V.p[i], x[i]); }   // half step x_i + alpha_i p_i
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             ++it;
-            o.nr = nq;
+            o.nr = qq;
             o.half = 1;
             o.status = PBCG_OK;
-            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = nq;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
             break;
         }
         omega = __ddiv_rn(qy, yy);
@@ -221,9 +262,9 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
         } else {
             // replacement, first part: x_{i+1}; r_{i+1} := b - A x_{i+1}; w_{i+1} := A r_{i+1}
             PBCG_ROWS(i) { x[i] = fma(omega, V.q[i], fma(alpha, V.p[i], x[i])); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) { V.r[i] = a.b[i] - A.row(i, VecLoad{x}); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const double wn = A.row(i, VecLoad{V.r});
                 const double rn = V.r[i], r0i = V.r0[i];
@@ -239,13 +280,13 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
         if (!grid_sum<3>(g, d2, sm, sflag)) return false;
         ++it;
         const double rho_n = d2[0], r0w = d2[1];
-        o.nr = sqrt(d2[2]);
-        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = o.nr;
-        if (!all_finite(d2, 3)) { o.status = PBCG_NONFINITE; break; }
-        if (!fixed && o.nr <= tol) { o.status = PBCG_OK; break; }
+        o.nr = d2[2];
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = d2[2];
+        if (!all_finite(d2)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && norm_below(d2[2], tol, tol2)) { o.status = PBCG_OK; break; }
         if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
         // beta_i = (alpha_i / omega_i) (r0, r_{i+1}) / (r0, r_i); alpha_{i+1} by eq. (3)
-        beta = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_n, rho));
+        beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
         const double den = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
         if (den == 0.0) { o.status = PBCG_BREAKDOWN; break; }
         alpha = __ddiv_rn(rho_n, den);
@@ -257,10 +298,10 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kTPB) pbicgstab_kernel(const Op A, const SolveArgs a) {
+__global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
-    GridSync g{a.ctl, a.partials, 0u, 0};
+    GridSync g{a.ctl, a.partials, 0u, 0};   // partials: the exchange slots
     const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
     Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
@@ -277,7 +318,7 @@ __global__ void __launch_bounds__(kTPB) pbicgstab_kernel(const Op A, const Solve
 template <class Op>
 __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
                                               int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
-    const Vectors V = a.V;
+    const Vectors &V = a.V;
     double *x = a.x;
     const bool fixed = a.fixed != 0;
     const bool v3 = a.variant == 3;
@@ -300,7 +341,7 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
     o.nr0 = sqrt(rho);
     o.nr = o.nr0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
-    const double tol = __dmul_rn(a.rtol, o.nr0);
+    const double tol = __dmul_rn(a.rtol, o.nr0), tol2 = __dmul_rn(tol, tol);
     if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
     double beta = 0.0, omega = 0.0;
 
@@ -318,7 +359,7 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
             }
         } else {
             PBCG_ROWS(i) { pA[i] = fma(beta, fma(-omega, sA[i], pA[i]), V.r[i]); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const double si = A.row(i, VecLoad{pA});
                 sA[i] = si;
@@ -347,7 +388,7 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
             }
         } else {
             PBCG_ROWS(i) { V.q[i] = fma(-alpha, sc[i], V.r[i]); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const double yi = A.row(i, VecLoad{V.q});
                 const double qi = V.q[i];
@@ -360,18 +401,17 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
         ++spmvs;
         if (!grid_sum<3>(g, d2, sm, sflag)) return false;
         const double qy = d2[0], yy = d2[1], qq = d2[2];
-        if (!all_finite(d2, 3)) { o.status = PBCG_NONFINITE; break; }
-        const double nq = sqrt(qq);
-        const bool small_q = !fixed && nq <= tol;
+        if (!all_finite(d2)) { o.status = PBCG_NONFINITE; break; }
+        const bool small_q = !fixed && norm_below(qq, tol, tol2);
         if (small_q || yy == 0.0) {
             if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
             PBCG_ROWS(i) { x[i] = fma(alpha, pc[i], x[i]); }
-            if (!grid_sync(g, sflag)) return false;
+            if (!grid_sync(g, sm, sflag)) return false;
             ++it;
-            o.nr = nq;
+            o.nr = qq;
             o.half = 1;
             o.status = PBCG_OK;
-            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = nq;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
             break;
         }
         omega = __ddiv_rn(qy, yy);
@@ -390,12 +430,12 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
         if (!grid_sum<2>(g, d3, sm, sflag)) return false;
         ++it;
         const double rho_n = d3[0];
-        o.nr = sqrt(d3[1]);
-        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = o.nr;
-        if (!all_finite(d3, 2)) { o.status = PBCG_NONFINITE; break; }
-        if (!fixed && o.nr <= tol) { o.status = PBCG_OK; break; }
+        o.nr = d3[1];
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = d3[1];
+        if (!all_finite(d3)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && norm_below(d3[1], tol, tol2)) { o.status = PBCG_OK; break; }
         if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
-        beta = __dmul_rn(__ddiv_rn(alpha, omega), __ddiv_rn(rho_n, rho));
+        beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
         rho = rho_n;
         if (v3) {
             double *tp = pA; pA = pB; pB = tp;
@@ -408,10 +448,10 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
 }
 
 template <class Op>
-__global__ void __launch_bounds__(kTPB) bicgstab_kernel(const Op A, const SolveArgs a) {
+__global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
-    GridSync g{a.ctl, a.partials, 0u, 0};
+    GridSync g{a.ctl, a.partials, 0u, 0};   // partials: the exchange slots
     const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
     Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};

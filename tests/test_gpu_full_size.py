@@ -58,7 +58,7 @@ def test_full_size_first_iterations(cfg2, form):
     x, info, hist = s.solve(dev(b), rtol=0.0, maxit=k, fixed_iters=k, history=True)
     assert info["status"] == native.PBCG_OK
     h = hist.cpu().numpy()
-    assert np.max(np.abs(h - ref.hist) / ref.hist) <= 1e-8
+    assert np.all(np.abs(h - ref.hist) <= 1e-8 * ref.hist + 1e-13 * ref.nr0)
     xg = x.cpu().numpy()
     assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-9
     s.close()

@@ -22,6 +22,14 @@ pytestmark = pytest.mark.gpu
 
 X_TOL = 1e-9
 HIST_TOL = 1e-8
+# Residual norms near the attainable-accuracy floor carry rounding noise of
+# order eps * ||A|| ||x||; below this floor (relative to ||r_0||) a relative
+# comparison of two norms says nothing, so an absolute floor is added.
+HIST_FLOOR = 1e-13
+
+
+def hist_close(h, hr, nr0):
+    return np.all(np.abs(h - hr) <= HIST_TOL * hr + HIST_FLOOR * nr0)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -118,8 +126,7 @@ def test_first_iterations_match_oracle(name, form, method, variant):
                             plain_variant=variant)
     assert info["status"] == native.PBCG_OK and info["iters"] == k
     assert rel(host(x), fx.x) <= X_TOL
-    h, hr = host(hist), fx.hist
-    assert np.max(np.abs(h - hr) / hr) <= HIST_TOL
+    assert hist_close(host(hist), fx.hist, fx.nr0)
     s.close()
 
 
@@ -161,17 +168,20 @@ def test_free_run_converges_like_oracle(name, method):
     s.close()
 
 
-@pytest.mark.parametrize("k", [3, 5, 10])
+@pytest.mark.parametrize("k", [2, 3, 4, 6])
 def test_residual_replacement_matches_oracle(k):
+    """12 iterations with a replacement every k (6, 4, 3 or 2 replacements);
+    each replacement recomputes b - A x, whose cancellation makes the two sides'
+    rounding differ more than an ordinary step, so the horizon is shorter."""
     s, A = solver_for("cd2d_64", "stencil")
     xs = P.splitmix64_uniform(0, A.n)
     b = oracle.spmv(A, xs)
-    steps = STEP_ITERS
+    steps = 12
     fx = oracle.pbicgstab(A, b, rtol=0.0, maxit=steps, fixed_iters=steps, replace_period=k)
     x, info, hist = s.solve(dev(b), rtol=0.0, maxit=steps, fixed_iters=steps, replace_period=k, history=True)
     assert info["n_replacements"] == fx.n_replacements == steps // k
     assert rel(host(x), fx.x) <= X_TOL
-    assert np.max(np.abs(host(hist) - fx.hist) / fx.hist) <= HIST_TOL
+    assert hist_close(host(hist), fx.hist, fx.nr0)
     s.close()
 
 

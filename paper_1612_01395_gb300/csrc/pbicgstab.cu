@@ -72,7 +72,8 @@ pbcg_status occupancy(int *pipe, int *plain) {
     return PBCG_OK;
 }
 
-pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, size_t ws_bytes, void *stream) {
+pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, size_t ws_bytes, void *stream,
+                        bool events = true) {
     if (prec != PBCG_PREC_NONE)
         return fail(PBCG_ERR_ARG, "preconditioner %d is not available (only PBCG_PREC_NONE)", (int)prec);
     if (!d_ws) return fail(PBCG_ERR_ARG, "workspace is NULL");
@@ -87,8 +88,10 @@ pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, s
     int coop = 0;
     PBCG_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device));
     if (!coop) return fail(PBCG_ERR_CUDA, "device does not support cooperative launches");
-    PBCG_CUDA(cudaEventCreate(&h->ev0));
-    PBCG_CUDA(cudaEventCreate(&h->ev1));
+    if (events) {
+        PBCG_CUDA(cudaEventCreate(&h->ev0));
+        PBCG_CUDA(cudaEventCreate(&h->ev1));
+    }
     h->ctl = (pbcg::Control *)h->ws;
     h->partials = (double *)(h->ws + pbcg::kControlBytes);
     double *v0 = (double *)(h->ws + pbcg::kControlBytes + pbcg::kPartialBytes);
@@ -159,13 +162,13 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
     // every exchange slot starts as the sentinel (all bits set)
     PBCG_CUDA(cudaMemsetAsync(h->partials, 0xFF, 3ull * grid * pbcg::kSlotDoubles * sizeof(double), h->stream));
-    PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
+    if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
     if (h->n > 0) {
         pbcg_status st = h->kind == 0 ? launch_solver(h, h->csr, pipelined, a, grid)
                                       : launch_solver(h, h->st, pipelined, a, grid);
         if (st != PBCG_OK) return st;
     }
-    PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
+    if (h->ev1) PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
     pbcg::Control c;
     PBCG_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     PBCG_CUDA(cudaStreamSynchronize(h->stream));
@@ -193,9 +196,28 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
         info->grid_syncs = c.grid_syncs;
         info->spmvs = c.spmvs;
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) info->kernel_ms = ms;
+        if (h->ev0 && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) info->kernel_ms = ms;
     }
     return st;
+}
+
+// CSR structure check on the device; the flag lives in the control block.
+pbcg_status check_csr(pbicgstab_s *h, int32_t n, int32_t nnz, const int32_t *d_rowptr, const int32_t *d_col) {
+    int *flag = &h->ctl->abort;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) {
+        int blocks = (int)(((long long)(nnz > n ? nnz : n) + 1 + 255) / 256);
+        if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+        if (blocks < 1) blocks = 1;
+        pbcg::csr_check_kernel<<<blocks, 256, 0, h->stream>>>(n, nnz, d_rowptr, d_col, flag);
+        e = cudaGetLastError();
+    }
+    int bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(PBCG_ERR_CUDA, "CSR check: %s", cudaGetErrorString(e));
+    if (bad) return fail(PBCG_ERR_ARG, "invalid CSR structure (check code %d)", bad);
+    return PBCG_OK;
 }
 
 }  // namespace
@@ -217,23 +239,7 @@ pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr
         h->csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
         st = occupancy<pbcg::CsrOp>(&h->occ_pipe, &h->occ_plain);
     }
-    if (st == PBCG_OK) {
-        // structure check on the device; the flag lives in the control block
-        int *flag = &h->ctl->abort;
-        cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), h->stream);
-        if (e == cudaSuccess) {
-            int blocks = (int)(((long long)(nnz > n ? nnz : n) + 1 + 255) / 256);
-            if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
-            if (blocks < 1) blocks = 1;
-            pbcg::csr_check_kernel<<<blocks, 256, 0, h->stream>>>(n, nnz, d_rowptr, d_col, flag);
-            e = cudaGetLastError();
-        }
-        int bad = 0;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) st = fail(PBCG_ERR_CUDA, "CSR check: %s", cudaGetErrorString(e));
-        else if (bad) st = fail(PBCG_ERR_ARG, "invalid CSR structure (check code %d)", bad);
-    }
+    if (st == PBCG_OK) st = check_csr(h, n, nnz, d_rowptr, d_col);
     if (st != PBCG_OK) {
         pbicgstab_destroy(h);
         return st;
@@ -353,3 +359,4 @@ void pbicgstab_destroy(pbicgstab_t h) {
 }
 
 }  // extern "C"
+

@@ -175,6 +175,33 @@ pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y);
 /* Number of unknowns of the handle. */
 int32_t pbicgstab_size(pbicgstab_t h);
 
+/* Largest system pbicgstab_solve_csr_noalloc accepts. */
+#define PBCG_NOALLOC_MAX_N 32768
+
+/* pbicgstab_solve for a CSR matrix without allocating anything and without a
+ * handle or workspace. The paper has no counterpart: this serves callers that
+ * may not allocate device memory or cannot provide a workspace -- e.g. code
+ * inside an application that owns all device memory and forbids allocation
+ * after start-up (cudaMalloc synchronises the device and can fail under
+ * pressure), real-time loops, or plug-ins that only get input and output
+ * pointers. Its scratch is a fixed array in the library's device memory sized
+ * for PBCG_NOALLOC_MAX_N unknowns (about 3.4 MB), which every GPU that loads
+ * the library keeps until the process exits.
+ *   Arguments as pbicgstab_create_csr + pbicgstab_solve (CSR validated on the
+ *   device each call; info->kernel_ms is 0). n > PBCG_NOALLOC_MAX_N returns
+ *   PBCG_ERR_ARG.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.
+ *   All calls on a device share the one array, and each call resets the parts
+ *   that must start from a known state. Calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race on it; serialise them.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+pbcg_status pbicgstab_solve_csr_noalloc(int32_t n, int32_t nnz, const int32_t *d_rowptr, const int32_t *d_col,
+                                        const double *d_val, const double *d_b, double *d_x, double rtol,
+                                        int32_t maxit, int32_t replace_period, const pbcg_opts *opts, void *stream,
+                                        pbcg_info *info);
+
 /* Release the handle (host memory only; the caller's buffers are untouched).
  * Synchronises the handle's stream first. NULL is ignored. */
 void pbicgstab_destroy(pbicgstab_t h);

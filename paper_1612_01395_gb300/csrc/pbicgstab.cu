@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "pbicgstab.h"
@@ -360,3 +361,73 @@ void pbicgstab_destroy(pbicgstab_t h) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Solve without any device allocation, for callers that may not allocate.
+//
+// Some callers cannot call cudaMalloc or hand the library a workspace: code
+// running inside a host application that owns all device memory and forbids
+// allocation after start-up (allocation synchronises the device and can fail
+// under memory pressure at a point the application cannot handle), real-time
+// loops that must not block on the allocator, and plug-ins that only receive
+// input and output pointers. For them the workspace of one solve lives in a
+// fixed array in this library's device memory, sized for at most
+// PBCG_NOALLOC_MAX_N unknowns; every GPU that loads the library keeps that
+// array (about 3.4 MB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = pbcg::kControlBytes + pbcg::kPartialBytes +
+                                 (size_t)kVectors * (((size_t)PBCG_NOALLOC_MAX_N + 31) / 32 * 32) * sizeof(double);
+
+// The shared scratch. Host code must not use this name as an address: it is a
+// host-side stand-in; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch on the current device; looked up once per
+// device, with that device current.
+pbcg_status noalloc_scratch(void **out) {
+    int dev = 0;
+    PBCG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(PBCG_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PBCG_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PBCG_OK;
+}
+
+}  // namespace
+
+extern "C" pbcg_status pbicgstab_solve_csr_noalloc(int32_t n, int32_t nnz, const int32_t *d_rowptr,
+                                                   const int32_t *d_col, const double *d_val, const double *d_b,
+                                                   double *d_x, double rtol, int32_t maxit, int32_t replace_period,
+                                                   const pbcg_opts *opts, void *stream, pbcg_info *info) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (n < 0 || nnz < 0) return fail(PBCG_ERR_ARG, "n and nnz must be >= 0");
+    if (n > PBCG_NOALLOC_MAX_N)
+        return fail(PBCG_ERR_ARG, "n = %d exceeds the no-allocation limit of %d unknowns", n, PBCG_NOALLOC_MAX_N);
+    if (!d_rowptr || (nnz > 0 && (!d_col || !d_val))) return fail(PBCG_ERR_ARG, "CSR array is NULL");
+    void *ws = nullptr;
+    pbcg_status st = noalloc_scratch(&ws);
+    if (st != PBCG_OK) return st;
+    pbicgstab_s h{};   // on the stack; no events (creating them is not needed here)
+    st = common_init(&h, n, PBCG_PREC_NONE, ws, kNoAllocBytes, stream, false);
+    if (st == PBCG_OK) {
+        h.kind = 0;
+        h.csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        st = occupancy<pbcg::CsrOp>(&h.occ_pipe, &h.occ_plain);
+    }
+    if (st == PBCG_OK) st = check_csr(&h, n, nnz, d_rowptr, d_col);
+    if (st != PBCG_OK) return st;
+    // run_solve clears the control block and the exchange slots before the launch
+    return run_solve(&h, true, d_b, d_x, rtol, maxit, replace_period, opts, info);
+}

@@ -30,7 +30,9 @@ PBCG_PREC_NONE, PBCG_PREC_JACOBI = 0, 1
 # Exported symbols, as declared in include/pbicgstab.h.
 EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_create_csr", "pbicgstab_create_stencil",
            "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
-           "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error"]
+           "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc"]
+# Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
+PBCG_NOALLOC_MAX_N = 32768
 
 
 class PbcgCoef(ctypes.Structure):
@@ -103,6 +105,8 @@ def lib():
         L.pbicgstab_solve_host.argtypes = [vp, i32, vp, vp, f64, i32, i32, ctypes.POINTER(PbcgOpts),
                                            ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_spmv.argtypes = [vp, vp, vp]
+        L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
+                                                  ctypes.POINTER(PbcgOpts), vp, ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_size.argtypes = [vp]
         L.pbicgstab_size.restype = i32
         L.pbicgstab_destroy.argtypes = [vp]
@@ -110,7 +114,7 @@ def lib():
         L.pbicgstab_last_error.argtypes = []
         L.pbicgstab_last_error.restype = ctypes.c_char_p
         for name in ("pbicgstab_create_csr", "pbicgstab_create_stencil", "pbicgstab_solve", "bicgstab_solve",
-                     "pbicgstab_solve_host", "pbicgstab_spmv"):
+                     "pbicgstab_solve_host", "pbicgstab_spmv", "pbicgstab_solve_csr_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -175,6 +179,18 @@ def pbicgstab_solve_host(h, method, h_b, h_x, rtol, maxit, replace_period=0, **o
     o = _opts(**opts)
     st = lib().pbicgstab_solve_host(h, int(method), h_b, h_x, float(rtol), int(maxit), int(replace_period),
                                     ctypes.byref(o), ctypes.byref(info))
+    return st, info
+
+
+def pbicgstab_solve_csr_noalloc(n, nnz, d_rowptr, d_col, d_val, d_b, d_x, rtol, maxit, replace_period, stream,
+                                **opts):
+    """Solve with a CSR matrix without any device allocation, for callers that
+    may not allocate (see include/pbicgstab.h); n <= PBCG_NOALLOC_MAX_N."""
+    info = PbcgInfo()
+    o = _opts(**opts)
+    st = lib().pbicgstab_solve_csr_noalloc(int(n), int(nnz), d_rowptr, d_col, d_val, d_b, d_x, float(rtol),
+                                           int(maxit), int(replace_period), ctypes.byref(o), stream,
+                                           ctypes.byref(info))
     return st, info
 
 

@@ -62,6 +62,9 @@ def lib():
         _lib.o_bicgstab.argtypes = common + [dp, dp, dp, ctypes.POINTER(OInfo)]
         _lib.o_cabicgstab.argtypes = common + [dp, dp, dp, ctypes.POINTER(OInfo)]
         _lib.o_pbicgstab.argtypes = common + [i32, i32, i32, i32, dp, dp, dp, dp, ctypes.POINTER(OInfo)]
+        pcommon = [i32, ip, ip, dp, dp, dp, dp, f64, i32, i32]
+        _lib.o_bicgstab_prec.argtypes = pcommon + [dp, dp, dp, ctypes.POINTER(OInfo)]
+        _lib.o_pbicgstab_prec.argtypes = pcommon + [i32, i32, dp, dp, dp, ctypes.POINTER(OInfo)]
     return _lib
 
 
@@ -146,6 +149,55 @@ def _run(method: str, A, b, x0, rtol, maxit, fixed_iters, trace, replace_period=
                   hist=hist[:k + 1].copy(),
                   trace_x=None if tx is None else tx[:k + 1].copy(),
                   trace_r=None if trr is None else trr[:k + 1].copy(), work=wd)
+
+
+def jacobi_minv(A) -> np.ndarray:
+    """1 / diag(A) for the Jacobi preconditioner (M = diag(A))."""
+    d = np.zeros(A.n)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    on = A.col == rows
+    d[rows[on]] = A.val[on]
+    return 1.0 / d
+
+
+def _run_prec(method, A, minv, b, x0, rtol, maxit, fixed_iters, trace, replace_period=0, max_replacements=-1):
+    rowptr, col, val = _csr_args(A)
+    n = A.n
+    minv = np.ascontiguousarray(minv, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    steps = fixed_iters if fixed_iters > 0 else maxit
+    hist = np.full(steps + 1, np.nan)
+    tx = np.full((steps + 1, n), np.nan) if trace else None
+    trr = np.full((steps + 1, n), np.nan) if trace else None
+    info = OInfo()
+    L = lib()
+    args = [n, _p(rowptr, ctypes.c_int32), _p(col, ctypes.c_int32), _p(val), _p(minv), _p(b), _p(x),
+            float(rtol), int(maxit), int(fixed_iters)]
+    if method == "bicgstab":
+        L.o_bicgstab_prec(*args, _p(hist), _p(tx), _p(trr), ctypes.byref(info))
+    else:
+        L.o_pbicgstab_prec(*args, int(replace_period), int(max_replacements), _p(hist), _p(tx), _p(trr),
+                           ctypes.byref(info))
+    k = info.iters
+    return Result(x=x, iters=k, status=info.status, half_step=bool(info.half_step),
+                  n_replacements=info.n_replacements, nr0=info.nr0, rel_res_rec=info.rel_res_rec,
+                  rel_res_true=info.rel_res_true, flops=info.flops, spmvs=info.spmvs, hist=hist[:k + 1].copy(),
+                  trace_x=None if tx is None else tx[:k + 1].copy(),
+                  trace_r=None if trr is None else trr[:k + 1].copy())
+
+
+def bicgstab_prec(A, minv, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False) -> Result:
+    """Algorithm 10 (preconditioned BiCGStab) with M^{-1} u = minv * u, plain FP64."""
+    return _run_prec("bicgstab", A, minv, b, x0, rtol, maxit, fixed_iters, trace)
+
+
+def pbicgstab_prec(A, minv, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False, replace_period=0,
+                   max_replacements=-1) -> Result:
+    """Algorithm 11 (preconditioned pipelined BiCGStab) with M^{-1} u = minv * u and residual
+    replacement every ``replace_period`` iterations, plain FP64."""
+    return _run_prec("pbicgstab", A, minv, b, x0, rtol, maxit, fixed_iters, trace, replace_period,
+                     max_replacements)
 
 
 def bicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False) -> Result:

@@ -487,3 +487,224 @@ out:
     free(mem);
     return info->status;
 }
+
+/* ===========================================================================
+ * Preconditioned variants (Section 3.6) with a diagonal preconditioner:
+ * M^{-1} u = minv .* u (Jacobi when minv = 1 / diag(A)). Right
+ * preconditioning: A M^{-1} y = b, x = M^{-1} y.
+ * ========================================================================= */
+static void prec(int32_t n, double *out, const double *minv, const double *in)
+{
+    for (int32_t i = 0; i < n; i++) out[i] = minv[i] * in[i];
+}
+
+/* Algorithm 10: preconditioned BiCGStab. */
+int o_bicgstab_prec(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *minv,
+                    const double *b, double *x, double rtol, int32_t maxit, int32_t fixed_iters,
+                    double *hist, double *trace_x, double *trace_r, o_info *info)
+{
+    o_csr A = {n, rowptr, col, val};
+    o_trace tr = {hist, trace_x, trace_r};
+    o_count cnt = {0.0, 0};
+    memset(info, 0, sizeof(*info));
+    if (n < 0 || maxit < 0 || !minv) return info->status = O_ERR_ARG;
+    double *mem = (double *)calloc((size_t)10 * (n > 0 ? n : 1), sizeof(double));
+    if (!mem) return info->status = O_ERR_OOM;
+    double *r = mem, *r0 = r + n, *p = r0 + n, *ph = p + n, *s = ph + n, *q = s + n, *qh = q + n, *y = qh + n,
+           *tmp = y + n;
+    int32_t limit = fixed_iters > 0 ? fixed_iters : maxit;
+
+    /* r_0 := b - A x_0; p_0 := r_0 */
+    spmv(&A, x, tmp, &cnt);
+    for (int32_t j = 0; j < n; j++) r[j] = b[j] - tmp[j];
+    memcpy(r0, r, sizeof(double) * n);
+    memcpy(p, r, sizeof(double) * n);
+    double rho = dot(n, r0, r, NULL);
+    double nr = norm2(n, r);
+    info->nr0 = nr;
+    record(&tr, 0, n, nr, x, r);
+    double tol = rtol * info->nr0;
+    info->status = O_NOT_CONVERGED;
+    if (info->nr0 == 0.0) { info->status = O_CONVERGED; finish(&A, b, x, tmp, nr, info, &cnt); free(mem); return info->status; }
+
+    int32_t i;
+    for (i = 0; i < limit; i++) {
+        /* p^_i := M^{-1} p_i; s_i := A p^_i */
+        prec(n, ph, minv, p);
+        spmv(&A, ph, s, &cnt);
+        double r0s = dot(n, r0, s, &cnt);
+        if (!isfinite(r0s)) { info->status = O_NONFINITE; break; }
+        if (r0s == 0.0) { info->status = O_BREAKDOWN; break; }
+        double alpha = rho / r0s;
+        /* q_i := r_i - alpha_i s_i; q^_i := M^{-1} q_i; y_i := A q^_i */
+        axpy(n, q, r, -alpha, s, &cnt);
+        prec(n, qh, minv, q);
+        spmv(&A, qh, y, &cnt);
+        double qy = dot(n, q, y, &cnt), yy = dot(n, y, y, &cnt), qq = dot(n, q, q, NULL);
+        double d1[3] = {qy, yy, qq};
+        if (!finite_all(3, d1)) { info->status = O_NONFINITE; break; }
+        if ((fixed_iters <= 0 && sqrt(qq) <= tol) || yy == 0.0) {
+            if (yy == 0.0 && qq != 0.0 && !(fixed_iters <= 0 && sqrt(qq) <= tol)) { info->status = O_BREAKDOWN; break; }
+            axpy(n, x, x, alpha, ph, &cnt);
+            nr = sqrt(qq);
+            info->half_step = 1;
+            info->status = O_CONVERGED;
+            record(&tr, i + 1, n, nr, x, q);
+            i++;
+            break;
+        }
+        double omega = qy / yy;
+        if (omega == 0.0) { info->status = O_BREAKDOWN; break; }
+        /* x_{i+1} := x_i + alpha_i p^_i + omega_i q^_i; r_{i+1} := q_i - omega_i y_i */
+        axpy(n, x, x, alpha, ph, &cnt);
+        axpy(n, x, x, omega, qh, &cnt);
+        axpy(n, r, q, -omega, y, &cnt);
+        double rho_new = dot(n, r0, r, &cnt);
+        double rr = dot(n, r, r, NULL);
+        double d2[2] = {rho_new, rr};
+        nr = sqrt(rr);
+        record(&tr, i + 1, n, nr, x, r);
+        if (!finite_all(2, d2)) { info->status = O_NONFINITE; i++; break; }
+        if (fixed_iters <= 0 && nr <= tol) { info->status = O_CONVERGED; i++; break; }
+        if (rho_new == 0.0) { info->status = O_BREAKDOWN; i++; break; }
+        double beta = (alpha / omega) * (rho_new / rho);
+        rho = rho_new;
+        /* p_{i+1} := r_{i+1} + beta_i (p_i - omega_i s_i) */
+        axpy(n, p, p, -omega, s, &cnt);
+        axpy(n, p, r, beta, p, &cnt);
+    }
+    if (fixed_iters > 0 && info->status == O_NOT_CONVERGED && i == limit) info->status = O_CONVERGED;
+    info->iters = i;
+    finish(&A, b, x, tmp, nr, info, &cnt);
+    free(mem);
+    return info->status;
+}
+
+/* Algorithm 11: preconditioned pipelined BiCGStab, with the residual
+ * replacement of Section 4.2 in the split placement used by o_pbicgstab:
+ * r_i := b - A x_i, r^_i := M^{-1} r_i, w_i := A r^_i before the second
+ * reduction of iteration i-1 (so w^_i = M^{-1} w_i and t_i = A w^_i follow
+ * from the replaced w_i), and s_i := A p^_i, s^_i := M^{-1} s_i,
+ * z_i := A s^_i after p^_i. 4 SpMVs and 2 preconditioner applications. */
+int o_pbicgstab_prec(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *minv,
+                     const double *b, double *x, double rtol, int32_t maxit, int32_t fixed_iters,
+                     int32_t replace_period, int32_t max_replacements,
+                     double *hist, double *trace_x, double *trace_r, o_info *info)
+{
+    o_csr A = {n, rowptr, col, val};
+    o_trace tr = {hist, trace_x, trace_r};
+    o_count cnt = {0.0, 0};
+    memset(info, 0, sizeof(*info));
+    if (n < 0 || maxit < 0 || !minv) return info->status = O_ERR_ARG;
+    double *mem = (double *)calloc((size_t)17 * (n > 0 ? n : 1), sizeof(double));
+    if (!mem) return info->status = O_ERR_OOM;
+    double *r = mem, *rh = r + n, *r0 = rh + n, *ph = r0 + n, *s = ph + n, *sh = s + n, *z = sh + n, *zh = z + n,
+           *q = zh + n, *qh = q + n, *y = qh + n, *w = y + n, *wh = w + n, *t = wh + n, *v = t + n, *tmp = v + n;
+    int32_t limit = fixed_iters > 0 ? fixed_iters : maxit;
+
+    /* r_0 := b - A x_0; r^_0 := M^{-1} r_0; w_0 := A r^_0; w^_0 := M^{-1} w_0; t_0 := A w^_0;
+     * alpha_0 := (r0, r0) / (r0, w0); beta_{-1} := 0 */
+    spmv(&A, x, tmp, &cnt);
+    for (int32_t j = 0; j < n; j++) r[j] = b[j] - tmp[j];
+    memcpy(r0, r, sizeof(double) * n);
+    prec(n, rh, minv, r);
+    spmv(&A, rh, w, &cnt);
+    prec(n, wh, minv, w);
+    spmv(&A, wh, t, &cnt);
+    double rho = dot(n, r0, r, NULL);
+    double r0w = dot(n, r0, w, NULL);
+    double nr = norm2(n, r);
+    info->nr0 = nr;
+    record(&tr, 0, n, nr, x, r);
+    double tol = rtol * info->nr0;
+    info->status = O_NOT_CONVERGED;
+    int32_t i = 0;
+    double alpha = 0.0, beta = 0.0, omega = 0.0;
+    int replaced = 0;
+    if (info->nr0 == 0.0) { info->status = O_CONVERGED; goto out; }
+    if (r0w == 0.0 || !isfinite(r0w)) { info->status = isfinite(r0w) ? O_BREAKDOWN : O_NONFINITE; goto out; }
+    alpha = rho / r0w;
+
+    for (i = 0; i < limit; i++) {
+        /* p^_i := r^_i + beta (p^_{i-1} - omega s^_{i-1}) */
+        axpy(n, ph, ph, -omega, sh, &cnt);
+        axpy(n, ph, rh, beta, ph, &cnt);
+        if (replaced) {
+            spmv(&A, ph, s, &cnt);
+            prec(n, sh, minv, s);
+            spmv(&A, sh, z, &cnt);
+        } else {
+            /* s_i := w_i + beta (s_{i-1} - omega z_{i-1}); s^_i := w^_i + beta (s^_{i-1} - omega z^_{i-1});
+             * z_i := t_i + beta (z_{i-1} - omega v_{i-1}) */
+            axpy(n, s, s, -omega, z, &cnt);
+            axpy(n, s, w, beta, s, &cnt);
+            axpy(n, sh, sh, -omega, zh, &cnt);
+            axpy(n, sh, wh, beta, sh, &cnt);
+            axpy(n, z, z, -omega, v, &cnt);
+            axpy(n, z, t, beta, z, &cnt);
+        }
+        /* q_i := r_i - alpha s_i; q^_i := r^_i - alpha s^_i; y_i := w_i - alpha z_i */
+        axpy(n, q, r, -alpha, s, &cnt);
+        axpy(n, qh, rh, -alpha, sh, &cnt);
+        axpy(n, y, w, -alpha, z, &cnt);
+        double qy = dot(n, q, y, &cnt), yy = dot(n, y, y, &cnt), qq = dot(n, q, q, NULL);
+        /* z^_i := M^{-1} z_i; v_i := A z^_i */
+        prec(n, zh, minv, z);
+        spmv(&A, zh, v, &cnt);
+        double d1[3] = {qy, yy, qq};
+        if (!finite_all(3, d1)) { info->status = O_NONFINITE; break; }
+        if ((fixed_iters <= 0 && sqrt(qq) <= tol) || yy == 0.0) {
+            if (yy == 0.0 && qq != 0.0 && !(fixed_iters <= 0 && sqrt(qq) <= tol)) { info->status = O_BREAKDOWN; break; }
+            axpy(n, x, x, alpha, ph, &cnt);
+            nr = sqrt(qq);
+            info->half_step = 1;
+            info->status = O_CONVERGED;
+            record(&tr, i + 1, n, nr, x, q);
+            i++;
+            break;
+        }
+        omega = qy / yy;
+        if (omega == 0.0) { info->status = O_BREAKDOWN; break; }
+        /* x_{i+1} := x_i + alpha p^_i + omega q^_i; r_{i+1} := q_i - omega y_i;
+         * r^_{i+1} := q^_i - omega (w^_i - alpha z^_i); w_{i+1} := y_i - omega (t_i - alpha v_i) */
+        axpy(n, x, x, alpha, ph, &cnt);
+        axpy(n, x, x, omega, qh, &cnt);
+        axpy(n, r, q, -omega, y, &cnt);
+        axpy(n, tmp, wh, -alpha, zh, &cnt);
+        axpy(n, rh, qh, -omega, tmp, &cnt);
+        axpy(n, tmp, t, -alpha, v, &cnt);
+        axpy(n, w, y, -omega, tmp, &cnt);
+        replaced = replace_period > 0 && (i + 1) % replace_period == 0 &&
+                   (max_replacements < 0 || info->n_replacements < max_replacements);
+        if (replaced) {
+            spmv(&A, x, tmp, &cnt);
+            for (int32_t j = 0; j < n; j++) r[j] = b[j] - tmp[j];
+            prec(n, rh, minv, r);
+            spmv(&A, rh, w, &cnt);
+            info->n_replacements++;
+        }
+        double rho_new = dot(n, r0, r, &cnt), r0w_new = dot(n, r0, w, &cnt);
+        double r0s = dot(n, r0, s, &cnt), r0z = dot(n, r0, z, &cnt);
+        double rr = dot(n, r, r, NULL);
+        /* w^_{i+1} := M^{-1} w_{i+1}; t_{i+1} := A w^_{i+1} */
+        prec(n, wh, minv, w);
+        spmv(&A, wh, t, &cnt);
+        double d2[5] = {rho_new, r0w_new, r0s, r0z, rr};
+        nr = sqrt(rr);
+        record(&tr, i + 1, n, nr, x, r);
+        if (!finite_all(5, d2)) { info->status = O_NONFINITE; i++; break; }
+        if (fixed_iters <= 0 && nr <= tol) { info->status = O_CONVERGED; i++; break; }
+        if (rho_new == 0.0) { info->status = O_BREAKDOWN; i++; break; }
+        beta = (alpha / omega) * (rho_new / rho);
+        double den = r0w_new + beta * r0s - beta * omega * r0z;
+        if (den == 0.0) { info->status = O_BREAKDOWN; i++; break; }
+        alpha = rho_new / den;
+        rho = rho_new;
+    }
+    if (fixed_iters > 0 && info->status == O_NOT_CONVERGED && i == limit) info->status = O_CONVERGED;
+out:
+    info->iters = i;
+    finish(&A, b, x, tmp, nr, info, &cnt);
+    free(mem);
+    return info->status;
+}

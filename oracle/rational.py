@@ -220,3 +220,129 @@ def pbicgstab(A, b, x0=None, maxit=50, replace_period=0, alpha_eq5=False, rr_pla
             alpha = rho_new / den
         rho = rho_new
     return dict(x=xs, r=rs, status="maxit", half_step=False, replacements=nrr)
+
+
+def _prec(minv, u: Vec) -> Vec:
+    return [m * e for m, e in zip(minv, u)]
+
+
+def bicgstab_prec(A, minv, b, x0=None, maxit=50):
+    """Algorithm 10 with M^{-1} u = minv * u (minv: Fractions)."""
+    n = len(b)
+    b = _vec(b)
+    minv = _vec(minv)
+    x = _vec(x0) if x0 is not None else [Fraction(0)] * n
+    r = lin(b, Fraction(-1), matvec(A, x))
+    r0 = list(r)
+    p = list(r)
+    rho = dot(r0, r)
+    xs, rs = [list(x)], [list(r)]
+    if _is_zero(r):
+        return dict(x=xs, r=rs, status="converged", half_step=False)
+    for _ in range(maxit):
+        ph = _prec(minv, p)
+        s = matvec(A, ph)
+        r0s = dot(r0, s)
+        if r0s == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False)
+        alpha = rho / r0s
+        q = lin(r, -alpha, s)
+        qh = _prec(minv, q)
+        y = matvec(A, qh)
+        qy, yy = dot(q, y), dot(y, y)
+        if yy == 0:
+            if not _is_zero(q):
+                return dict(x=xs, r=rs, status="breakdown", half_step=False)
+            x = lin(x, alpha, ph)
+            xs.append(list(x)); rs.append(list(q))
+            return dict(x=xs, r=rs, status="converged", half_step=True)
+        omega = qy / yy
+        if omega == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False)
+        x = lin(lin(x, alpha, ph), omega, qh)
+        r = lin(q, -omega, y)
+        xs.append(list(x)); rs.append(list(r))
+        if _is_zero(r):
+            return dict(x=xs, r=rs, status="converged", half_step=False)
+        rho_new = dot(r0, r)
+        if rho_new == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False)
+        beta = (alpha / omega) * (rho_new / rho)
+        rho = rho_new
+        p = lin(r, beta, lin(p, -omega, s))
+    return dict(x=xs, r=rs, status="maxit", half_step=False)
+
+
+def pbicgstab_prec(A, minv, b, x0=None, maxit=50, replace_period=0):
+    """Algorithm 11 with M^{-1} u = minv * u and residual replacement (split placement)."""
+    n = len(b)
+    b = _vec(b)
+    minv = _vec(minv)
+    x = _vec(x0) if x0 is not None else [Fraction(0)] * n
+    r = lin(b, Fraction(-1), matvec(A, x))
+    r0 = list(r)
+    rh = _prec(minv, r)
+    w = matvec(A, rh)
+    wh = _prec(minv, w)
+    t = matvec(A, wh)
+    zero = [Fraction(0)] * n
+    ph, s, sh, z, zh, v = (list(zero) for _ in range(6))
+    xs, rs = [list(x)], [list(r)]
+    if _is_zero(r):
+        return dict(x=xs, r=rs, status="converged", half_step=False, replacements=0)
+    rho = dot(r0, r)
+    if dot(r0, w) == 0:
+        return dict(x=xs, r=rs, status="breakdown", half_step=False, replacements=0)
+    alpha, beta, omega = rho / dot(r0, w), Fraction(0), Fraction(0)
+    nrr = 0
+    replaced = False
+    for i in range(maxit):
+        ph = lin(rh, beta, lin(ph, -omega, sh))
+        if replaced:
+            s = matvec(A, ph)
+            sh = _prec(minv, s)
+            z = matvec(A, sh)
+        else:
+            s = lin(w, beta, lin(s, -omega, z))
+            sh = lin(wh, beta, lin(sh, -omega, zh))
+            z = lin(t, beta, lin(z, -omega, v))
+        q = lin(r, -alpha, s)
+        qh = lin(rh, -alpha, sh)
+        y = lin(w, -alpha, z)
+        qy, yy = dot(q, y), dot(y, y)
+        zh = _prec(minv, z)
+        v = matvec(A, zh)
+        if yy == 0:
+            if not _is_zero(q):
+                return dict(x=xs, r=rs, status="breakdown", half_step=False, replacements=nrr)
+            x = lin(x, alpha, ph)
+            xs.append(list(x)); rs.append(list(q))
+            return dict(x=xs, r=rs, status="converged", half_step=True, replacements=nrr)
+        omega = qy / yy
+        if omega == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False, replacements=nrr)
+        x = lin(lin(x, alpha, ph), omega, qh)
+        r = lin(q, -omega, y)
+        rh = lin(qh, -omega, lin(wh, -alpha, zh))
+        w = lin(y, -omega, lin(t, -alpha, v))
+        replaced = replace_period > 0 and (i + 1) % replace_period == 0
+        if replaced:
+            r = lin(b, Fraction(-1), matvec(A, x))
+            rh = _prec(minv, r)
+            w = matvec(A, rh)
+            nrr += 1
+        rho_new, r0w, r0s, r0z = dot(r0, r), dot(r0, w), dot(r0, s), dot(r0, z)
+        wh = _prec(minv, w)
+        t = matvec(A, wh)
+        xs.append(list(x)); rs.append(list(r))
+        if _is_zero(r):
+            return dict(x=xs, r=rs, status="converged", half_step=False, replacements=nrr)
+        if rho_new == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False, replacements=nrr)
+        beta = (alpha / omega) * (rho_new / rho)
+        den = r0w + beta * r0s - beta * omega * r0z
+        if den == 0:
+            return dict(x=xs, r=rs, status="breakdown", half_step=False, replacements=nrr)
+        alpha = rho_new / den
+        rho = rho_new
+    return dict(x=xs, r=rs, status="maxit", half_step=False, replacements=nrr)

@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="grid points per axis")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--mixed-n", type=int, default=192, help="grid points per axis of the mixed-precision case")
     return ap.parse_args()
 
 
@@ -264,6 +266,56 @@ def summarize(elapsed, infos, steps):
             "grid_syncs": infos[0]["grid_syncs"], "spmvs": infos[0]["spmvs"], "grid": infos[0]["grid"]}
 
 
+def mixed_precision_case(n, steps, barrier):
+    """FP64 refinement around FP32 (and BF16-valued) Algorithm 9 against all-FP64
+    p-BiCGStab, both to a true relative residual of 1e-10, on the n^3
+    convection-diffusion system in CSR form."""
+    import torch
+    from paper_1612_01395_gb300 import native, problems as P
+    st = P.cd3d_trig(n)
+    A = P.stencil_to_csr(st)
+    N = A.n
+    s = native.Solver.from_csr(A)
+    bd = s.spmv(torch.from_numpy(P.splitmix64_uniform(SEED, N)).cuda())
+    v32 = torch.as_tensor(A.val).cuda().to(torch.float32)
+    v16 = torch.as_tensor(A.val).cuda().to(torch.bfloat16)
+    out = {"workload": f"3-D convection-diffusion {n}^3 (n={N}), CSR (nnz={A.nnz}), true rel.res 1e-10"}
+    runs = {}
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            res = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / k, res
+
+    k = max(1, min(steps, 3))
+    sec, (x64, i64) = timed(lambda: s.solve(bd, rtol=1e-10, maxit=MAXIT, replace_period=REPLACE_PERIOD), k)
+    runs["fp64_pbicgstab"] = {"value": sec, "iters": i64["iters"], "rel_res_true": i64["rel_res_true"],
+                              "status": native.STATUS_NAMES[i64["status"]]}
+    for name, vals, typ in (("mixed_fp32", v32, native.PBCG_VALUES_F32), ("mixed_bf16", v16, native.PBCG_VALUES_BF16)):
+        try:
+            sec, (xm, im) = timed(lambda: s.solve_mixed(bd, vals, typ, rtol=1e-10, max_outer=30, inner_rtol=1e-3,
+                                                        inner_maxit=4000), k)
+        except native.PbcgError as e:
+            runs[name] = {"error": str(e)}
+            continue
+        err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+        inner_bytes = (24 * 4 + 2 * (8 * A.nnz / N + 4)) * N   # FP32 vectors + FP32 CSR, per inner iteration
+        runs[name] = {"value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"],
+                      "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
+                      "rel_error_vs_fp64": err, "speedup_vs_fp64": runs["fp64_pbicgstab"]["value"] / sec,
+                      "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
+    s.close()
+    out.update(runs)
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -349,6 +401,9 @@ def run_ours(args):
             cmp_csr["pbicgstab" if method == "pipelined" else "bicgstab"] = r
         out["csr"] = cmp_csr
         csolver.close()
+
+    if not args.no_mixed:
+        out["mixed_precision"] = mixed_precision_case(args.mixed_n, args.steps, barrier)
 
     # end to end through the host-buffer C entry point: H2D b and x0, solve, D2H x
     hb = torch.from_numpy(bd.cpu().numpy()).pin_memory()

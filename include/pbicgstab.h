@@ -175,6 +175,42 @@ pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y);
 /* Number of unknowns of the handle. */
 int32_t pbicgstab_size(pbicgstab_t h);
 
+/* Result summary of pbicgstab_solve_mixed. */
+typedef struct {
+    int32_t outer;            /* refinement steps performed (inner solves) */
+    int32_t inner_iters;      /* inner iterations summed over all steps */
+    int32_t status;           /* PBCG_OK once ||b - A x|| <= rtol ||b - A x0|| in FP64 */
+    int32_t grid;             /* thread blocks used */
+    double nr0;               /* ||b - A x0||_2 */
+    double rel_res_true;      /* ||b - A x||_2 / ||b - A x0||_2 at exit, in FP64 */
+    int32_t grid_syncs;       /* device-wide synchronisations performed */
+    int32_t spmvs;            /* sparse matrix-vector products (FP64 and low precision) */
+    float kernel_ms;          /* duration of the solve kernel, CUDA events on the handle's stream */
+    int32_t pad;
+} pbcg_mixed_info;
+
+/* Low-precision value types for pbicgstab_solve_mixed. */
+enum { PBCG_VALUES_F32 = 0, PBCG_VALUES_BF16 = 1 };
+
+/* Mixed-precision solve (an extension of the paper's method, which states no
+ * precision): FP64 iterative refinement around pipelined BiCGStab
+ * (Algorithm 9) run on FP32 vectors. Each step computes r = b - A x with the
+ * handle's FP64 CSR matrix, solves A d = r with the FP32 pipelined iteration
+ * to ||r_inner|| <= inner_rtol ||r|| (at most inner_maxit iterations) on the
+ * low-precision copy of A's values, and sets x := x + d in FP64. Dot products
+ * that set alpha, beta and omega are accumulated in FP64. Stops when the FP64
+ * residual satisfies ||b - A x|| <= rtol ||b - A x0|| or after max_outer steps
+ * (PBCG_NOT_CONVERGED).
+ *   h            a CSR handle (PBCG_ERR_ARG for a stencil handle)
+ *   d_val_lowp   nnz values of the same CSR structure as float
+ *                (PBCG_VALUES_F32) or bfloat16 (PBCG_VALUES_BF16), caller-owned
+ *   opts         NULL or options; d_history (max_outer + 1 doubles) receives
+ *                the FP64 residual norm before each step; grid as for solve
+ * Uses the handle's workspace (no extra memory). */
+pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lowp, int32_t lowp_type, const double *d_b,
+                                  double *d_x, double rtol, int32_t max_outer, double inner_rtol,
+                                  int32_t inner_maxit, const pbcg_opts *opts, pbcg_mixed_info *info);
+
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
 #define PBCG_NOALLOC_MAX_N 32768
 

@@ -21,12 +21,12 @@ struct Control {
     int abort;               // nonzero: pbcg_status that stopped the launch
     int pad0[14];
     // result, written by block 0 at the end of a solve
-    int iters, status, half_step, n_repl, grid_syncs, spmvs, pad1[2];
+    int iters, status, half_step, n_repl, grid_syncs, spmvs, inner_iters, pad1;
     double nr0, rel_rec, rel_true, pad2;
 };
 static_assert(sizeof(Control) <= 256, "control block must fit 256 bytes");
 constexpr size_t kControlBytes = 256;
-constexpr size_t kPartialBytes = 3ull * kMaxGrid * 8 * sizeof(double);   // 3 rotating slot buffers
+constexpr size_t kPartialBytes = 3ull * kMaxGrid * 8 * sizeof(double);   // 3 rotating slot buffers of 8 doubles
 
 // n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply-high: the
 // round-up method of Granlund & Montgomery, "Division by invariant integers
@@ -131,19 +131,16 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double (*sm)[32]) {
 
 // Grid-wide exchange of a cooperative launch. Each block owns one 64-byte
 // slot (8 doubles) in each of 3 rotating buffers; exchange number e uses
-// buffer e % 3. A block publishes by (1) resetting its slot of buffer
-// (e+1) % 3 to the sentinel, (2) a gpu-scope fence, which orders every store
-// of the phase (made visible to thread 0 by __syncthreads) before (3) the
-// relaxed stores of its K partial sums into its slot of buffer e % 3. The
-// partial sums are the arrival signal: a reader polls each slot until none of
-// its K words is the sentinel, then fences (acquire) -- so one round trip
-// delivers both "everyone has arrived" and the data. The reset in (1) is safe:
-// buffer (e+1) % 3 last held exchange e-2, which every block has finished
-// reading before it published exchange e-1, which this block has seen.
-// Every wait is bounded (kSyncTimeoutNs) and watches the abort flag.
-// The host fills all slots with the sentinel before each launch.
-constexpr unsigned long long kSentinel = 0xFFFFFFFFFFFFFFFFull;   // a NaN that arithmetic never produces
-constexpr unsigned long long kQuietNaN = 0x7FF8000000000000ull;
+// buffer e % 3. Thread 0 of a block stores its K partial sums in its slot,
+// fences (gpu scope: every store of the phase, made visible to thread 0 by
+// __syncthreads, is ordered before the arrival), adds 1 to the arrival
+// counter, and spins on the counter until all blocks of exchange e arrived;
+// then every thread reads the slots. One poller per block on one word: polling
+// all slots from every thread congests the L2 and was measured slower. The
+// rotation keeps a slot from being rewritten while a slow block may still read
+// it (a block writes exchange e+3 only after all blocks arrived at e+2, i.e.
+// after all finished reading exchange e). Every wait is bounded
+// (kSyncTimeoutNs) and watches the abort flag.
 constexpr int kSlotDoubles = 8;
 
 struct GridSync {
@@ -153,15 +150,6 @@ struct GridSync {
     int count;          // exchanges performed (for diagnostics)
 };
 
-__device__ __forceinline__ void st_relaxed_u64(double *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ double *slot_ptr(const GridSync &g, unsigned buf, int block) {
     return g.slots + ((size_t)buf * gridDim.x + block) * kSlotDoubles;
 }
@@ -170,51 +158,33 @@ __device__ __forceinline__ double *slot_ptr(const GridSync &g, unsigned buf, int
 // acc receives, per thread, the fixed-order sum of slots tid, tid+kTPB, ...
 template <int K>
 __device__ __forceinline__ bool exchange(GridSync &g, const double (&mine)[K], double (&acc)[K], int *sflag) {
-    const unsigned buf = g.epoch % 3u, next = (g.epoch + 1u) % 3u;
+    const unsigned buf = g.epoch % 3u;
     if (threadIdx.x == 0) {
-        double *reset = slot_ptr(g, next, blockIdx.x);
-#pragma unroll
-        for (int k = 0; k < kSlotDoubles; ++k) reset[k] = __longlong_as_double((long long)kSentinel);
-        __threadfence();
         double *out = slot_ptr(g, buf, blockIdx.x);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            unsigned long long bits = (unsigned long long)__double_as_longlong(mine[k]);
-            st_relaxed_u64(out + k, bits == kSentinel ? kQuietNaN : bits);
+        for (int k = 0; k < K; ++k) out[k] = mine[k];
+        __threadfence();
+        atomicAdd(&g.ctl->arrivals, 1u);
+        const unsigned target = (g.epoch + 1u) * gridDim.x;
+        const uint64_t t0 = globaltimer_ns();
+        while (ld_acquire_u32(&g.ctl->arrivals) < target) {
+            if (ld_relaxed_s32(&g.ctl->abort) != 0) { *sflag = 0; break; }
+            if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
+                atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
+                *sflag = 0;
+                break;
+            }
         }
+        __threadfence();
     }
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    bool ok = true;
-    const uint64_t t0 = globaltimer_ns();
-    for (int b = threadIdx.x; b < (int)gridDim.x && ok; b += kTPB) {
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kTPB) {
         const double *src = slot_ptr(g, buf, b);
-        unsigned long long w[K];
-        unsigned spins = 0;
-        for (;;) {
-            bool ready = true;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                w[k] = ld_relaxed_u64(src + k);
-                ready = ready && w[k] != kSentinel;
-            }
-            if (ready) break;
-            if ((++spins & 63u) == 0) {
-                if (ld_relaxed_s32(&g.ctl->abort) != 0) { ok = false; break; }
-                if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
-                    atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
-                    ok = false;
-                    break;
-                }
-            }
-        }
-        if (!ok) break;
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __longlong_as_double((long long)w[k]);
+        for (int k = 0; k < K; ++k) acc[k] += __ldcg(src + k);
     }
-    __threadfence();   // acquire: later loads of this thread see what the publishers stored
-    if (!ok) *sflag = 0;
-    __syncthreads();
     const bool all_ok = *sflag != 0;
     g.epoch++;
     g.count++;

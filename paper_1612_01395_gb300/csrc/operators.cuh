@@ -10,15 +10,31 @@
 // assembly give bitwise identical rows. Products are accumulated with FMA.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "device_common.cuh"
 
 namespace pbcg {
 
+// fma for the arithmetic type of a sweep (FP64 path, or FP32 inner solves).
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+// A stored matrix value as the arithmetic type T of a sweep.
+template <typename T>
+__device__ __forceinline__ T value_as(double v) { return (T)v; }
+template <typename T>
+__device__ __forceinline__ T value_as(float v) { return (T)v; }
+template <typename T>
+__device__ __forceinline__ T value_as(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
+
 // u_j = x[j]
-struct VecLoad {
-    const double *x;
-    __device__ __forceinline__ double operator()(int j) const { return x[j]; }
+template <typename T>
+struct VecLoadT {
+    const T *x;
+    __device__ __forceinline__ T operator()(int j) const { return x[j]; }
 };
+using VecLoad = VecLoadT<double>;
 
 // u_j = r_j + beta (p_j - omega s_j): the p-recurrence of Algorithm 7
 struct PLoad {
@@ -34,20 +50,25 @@ struct QLoad {
     __device__ __forceinline__ double operator()(int j) const { return fma(-alpha, s[j], r[j]); }
 };
 
-struct CsrOp {
+// CSR with values stored as V (double; float or bfloat16 for low-precision
+// inner solves). A row is accumulated in the loader's type.
+template <typename V>
+struct CsrOpT {
     int n;
     const int *__restrict__ rowptr;
     const int *__restrict__ col;
-    const double *__restrict__ val;
+    const V *__restrict__ val;
 
     template <class L>
-    __device__ __forceinline__ double row(int r, const L &u) const {
+    __device__ __forceinline__ auto row(int r, const L &u) const -> decltype(u(0)) {
+        using T = decltype(u(0));
         const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
-        double acc = 0.0;
-        for (int k = b; k < e; ++k) acc = fma(__ldg(val + k), u(__ldg(col + k)), acc);
+        T acc = T(0);
+        for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(__ldg(col + k)), acc);
         return acc;
     }
 };
+using CsrOp = CsrOpT<double>;
 
 // One coefficient: t1[i*a1 + j*b1 + k*c1] (or `value` when t1 is null) plus
 // t2[i*a2 + j*b2 + k*c2] when t2 is set. Indices fit 31 bits (checked at create).

@@ -112,8 +112,10 @@ int pick_grid(const pbicgstab_s *h, int occ, int req) {
     int max_grid = occ * h->num_sms;
     if (max_grid > pbcg::kMaxGrid) max_grid = pbcg::kMaxGrid;
     if (req > 0) return req < max_grid ? req : max_grid;
-    // at least 32 rows per block; all co-resident blocks for large n
-    long long want = ((long long)h->n + 31) / 32;
+    // one row per thread while that leaves blocks to spare (small n: fewer
+    // blocks make each grid-wide exchange cheaper and the FP64 work per warp
+    // is the same); all co-resident blocks for large n
+    long long want = ((long long)h->n + pbcg::kTPB - 1) / pbcg::kTPB;
     if (want < 1) want = 1;
     return (int)(want < max_grid ? want : max_grid);
 }
@@ -161,8 +163,6 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
 
     const int grid = pick_grid(h, pipelined ? h->occ_pipe : h->occ_plain, o.grid);
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
-    // every exchange slot starts as the sentinel (all bits set)
-    PBCG_CUDA(cudaMemsetAsync(h->partials, 0xFF, 3ull * grid * pbcg::kSlotDoubles * sizeof(double), h->stream));
     if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
     if (h->n > 0) {
         pbcg_status st = h->kind == 0 ? launch_solver(h, h->csr, pipelined, a, grid)
@@ -362,6 +362,101 @@ void pbicgstab_destroy(pbicgstab_t h) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Mixed precision (FP64 refinement around FP32 pipelined BiCGStab).
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class Op32>
+pbcg_status launch_mixed(pbicgstab_s *h, const Op32 &a32, const pbcg::MixedArgs &m, int req_grid, int *grid_out) {
+    int occ = 0;
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::mixed_kernel<pbcg::CsrOp, Op32>, pbcg::kTPB, 0));
+    if (occ < 1) return fail(PBCG_ERR_CUDA, "mixed-precision kernel cannot be resident on an SM");
+    const int grid = pick_grid(h, occ, req_grid);
+    *grid_out = grid;
+    PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
+    if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
+    void *params[3] = {(void *)&h->csr, (void *)&a32, (void *)&m};
+    PBCG_CUDA(cudaLaunchCooperativeKernel((const void *)pbcg::mixed_kernel<pbcg::CsrOp, Op32>, dim3(grid),
+                                          dim3(pbcg::kTPB), params, 0, h->stream));
+    if (h->ev1) PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
+    return PBCG_OK;
+}
+
+}  // namespace
+
+extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lowp, int32_t lowp_type,
+                                             const double *d_b, double *d_x, double rtol, int32_t max_outer,
+                                             double inner_rtol, int32_t inner_maxit, const pbcg_opts *opts,
+                                             pbcg_mixed_info *info) {
+    if (info) memset(info, 0, sizeof(*info));
+    if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
+    if (h->kind != 0) return fail(PBCG_ERR_ARG, "mixed precision needs a CSR handle");
+    if (lowp_type != PBCG_VALUES_F32 && lowp_type != PBCG_VALUES_BF16)
+        return fail(PBCG_ERR_ARG, "lowp_type must be PBCG_VALUES_F32 or PBCG_VALUES_BF16");
+    if (h->n > 0 && (!d_b || !d_x)) return fail(PBCG_ERR_ARG, "b or x is NULL");
+    if (h->n > 0 && !d_val_lowp) return fail(PBCG_ERR_ARG, "low-precision values are NULL");
+    if (!(rtol >= 0.0) || !(inner_rtol >= 0.0)) return fail(PBCG_ERR_ARG, "tolerances must be >= 0");
+    if (max_outer < 0 || inner_maxit < 1) return fail(PBCG_ERR_ARG, "max_outer >= 0 and inner_maxit >= 1 required");
+    pbcg_opts o{-1, 0, nullptr, 0, 0};
+    if (opts) o = *opts;
+    if (o.grid < 0) return fail(PBCG_ERR_ARG, "grid must be >= 0");
+    if (h->n == 0) {
+        if (info) info->status = PBCG_OK;
+        return PBCG_OK;
+    }
+    // 12 float vectors carved from the FP64 vector area of the workspace
+    float *f0 = (float *)h->V.r;
+    const size_t s = vec_stride(h->n);
+    pbcg::MixedArgs m;
+    m.n = h->n;
+    m.b = d_b;
+    m.x = d_x;
+    float **slots[10] = {&m.V.r, &m.V.r0, &m.V.p, &m.V.s, &m.V.z, &m.V.q, &m.V.y, &m.V.w, &m.V.t, &m.V.v};
+    for (int k = 0; k < 10; ++k) *slots[k] = f0 + (size_t)k * s;
+    m.d = f0 + 10 * s;
+    m.rhs = f0 + 11 * s;
+    m.ctl = h->ctl;
+    m.partials = h->partials;
+    m.hist = o.d_history;
+    m.rtol = rtol;
+    m.max_outer = max_outer;
+    m.inner_rtol = inner_rtol;
+    m.inner_maxit = inner_maxit;
+    int grid = 0;
+    pbcg_status st;
+    if (lowp_type == PBCG_VALUES_F32) {
+        const pbcg::CsrOpT<float> a32{h->n, h->csr.rowptr, h->csr.col, (const float *)d_val_lowp};
+        st = launch_mixed(h, a32, m, o.grid, &grid);
+    } else {
+        const pbcg::CsrOpT<__nv_bfloat16> a16{h->n, h->csr.rowptr, h->csr.col, (const __nv_bfloat16 *)d_val_lowp};
+        st = launch_mixed(h, a16, m, o.grid, &grid);
+    }
+    if (st != PBCG_OK) return st;
+    pbcg::Control c;
+    PBCG_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    PBCG_CUDA(cudaStreamSynchronize(h->stream));
+    if (c.abort != 0) {
+        st = fail((pbcg_status)c.abort, "solver aborted: a grid-wide synchronisation timed out");
+        c.status = c.abort;
+    } else {
+        st = (pbcg_status)c.status;
+    }
+    if (info) {
+        info->outer = c.iters;
+        info->inner_iters = c.inner_iters;
+        info->status = c.status;
+        info->grid = grid;
+        info->nr0 = c.nr0;
+        info->rel_res_true = c.rel_true;
+        info->grid_syncs = c.grid_syncs;
+        info->spmvs = c.spmvs;
+        float ms = 0.0f;
+        if (h->ev0 && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) info->kernel_ms = ms;
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // Solve without any device allocation, for callers that may not allocate.
 //
 // Some callers cannot call cudaMalloc or hand the library a workspace: code
@@ -428,6 +523,6 @@ extern "C" pbcg_status pbicgstab_solve_csr_noalloc(int32_t n, int32_t nnz, const
     }
     if (st == PBCG_OK) st = check_csr(&h, n, nnz, d_rowptr, d_col);
     if (st != PBCG_OK) return st;
-    // run_solve clears the control block and the exchange slots before the launch
+    // run_solve clears the control block before the launch
     return run_solve(&h, true, d_b, d_x, rtol, maxit, replace_period, opts, info);
 }

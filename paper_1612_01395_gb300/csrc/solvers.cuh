@@ -21,15 +21,18 @@
 
 namespace pbcg {
 
-struct Vectors {
-    double *r, *r0, *p, *s, *z, *q, *y, *w, *t, *v;
+template <typename T>
+struct VectorsT {
+    T *r, *r0, *p, *s, *z, *q, *y, *w, *t, *v;
 };
+using Vectors = VectorsT<double>;
 
-struct SolveArgs {
+template <typename T>
+struct SolveArgsT {
     int n;
-    const double *b;
-    double *x;
-    Vectors V;
+    const T *b;
+    T *x;
+    VectorsT<T> V;
     Control *ctl;
     double *partials;
     double *hist;       // nullable
@@ -40,6 +43,7 @@ struct SolveArgs {
     int max_repl;       // < 0: unlimited
     int variant;        // Algorithm 7 only: 3 or 5
 };
+using SolveArgs = SolveArgsT<double>;
 
 // Resident blocks per SM the solver kernels are compiled for (register cap
 // 65536 / (kTPB * kMinBlocks)): the large-n sweeps are limited by the FP64 pipe,
@@ -126,24 +130,28 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
 // Section 4.2 (r := b - A x, w := A r before the second reduction of iteration
 // i-1; s := A p, z := A s after p_i; for i mod k == 0).
 // ===========================================================================
-template <class Op>
-__device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+// T is the vector and sweep arithmetic type: double for the FP64 solver,
+// float for the inner solves of the mixed-precision refinement. Dot products
+// are always accumulated in double, and alpha, beta, omega, rho are doubles;
+// a sweep uses them rounded to T.
+template <class Op, typename T>
+__device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> &a, GridSync &g, double (*sm)[32],
                                                int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
-    const Vectors &V = a.V;
-    double *x = a.x;
+    const VectorsT<T> &V = a.V;
+    T *x = a.x;
     const bool fixed = a.fixed != 0;
 
     // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
     double d0[1] = {0.0};
     PBCG_ROWS(i) {
-        const double ri = a.b[i] - A.row(i, VecLoad{x});
+        const T ri = a.b[i] - A.row(i, VecLoadT<T>{x});
         V.r[i] = ri;
         V.r0[i] = ri;
-        V.p[i] = 0.0;
-        V.s[i] = 0.0;
-        V.z[i] = 0.0;
-        V.v[i] = 0.0;
-        d0[0] = fma(ri, ri, d0[0]);
+        V.p[i] = T(0);
+        V.s[i] = T(0);
+        V.z[i] = T(0);
+        V.v[i] = T(0);
+        d0[0] = fma((double)ri, (double)ri, d0[0]);
     }
     ++spmvs;
     if (!grid_sum<1>(g, d0, sm, sflag)) return false;
@@ -157,9 +165,9 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
     // w_0 := A r_0; alpha_0 := (r0, r0) / (r0, w0)
     d0[0] = 0.0;
     PBCG_ROWS(i) {
-        const double wi = A.row(i, VecLoad{V.r});
+        const T wi = A.row(i, VecLoadT<T>{V.r});
         V.w[i] = wi;
-        d0[0] = fma(V.r0[i], wi, d0[0]);
+        d0[0] = fma((double)V.r0[i], (double)wi, d0[0]);
     }
     ++spmvs;
     if (!grid_sum<1>(g, d0, sm, sflag)) return false;
@@ -172,52 +180,53 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
     while (it < a.limit) {
         // ---- phase A: t_i = A w_i; p_i, s_i, z_i, q_i, y_i; first reduction
         double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
+        const T al = (T)alpha, be = (T)beta, om = (T)omega;
         if (!replaced_rw) {
             PBCG_ROWS(i) {
-                const double ti = A.row(i, VecLoad{V.w});
-                const double ri = V.r[i], wi = V.w[i], si = V.s[i], zi = V.z[i];
-                const double pn = fma(beta, fma(-omega, si, V.p[i]), ri);   // p_i
-                const double sn = fma(beta, fma(-omega, zi, si), wi);       // s_i, eq. (1)
-                const double zn = fma(beta, fma(-omega, V.v[i], zi), ti);   // z_i, eq. (6)
-                const double qi = fma(-alpha, sn, ri);                      // q_i
-                const double yi = fma(-alpha, zn, wi);                      // y_i, eq. (4)
+                const T ti = A.row(i, VecLoadT<T>{V.w});
+                const T ri = V.r[i], wi = V.w[i], si = V.s[i], zi = V.z[i];
+                const T pn = fmaT(be, fmaT(-om, si, V.p[i]), ri);   // p_i
+                const T sn = fmaT(be, fmaT(-om, zi, si), wi);       // s_i, eq. (1)
+                const T zn = fmaT(be, fmaT(-om, V.v[i], zi), ti);   // z_i, eq. (6)
+                const T qi = fmaT(-al, sn, ri);                     // q_i
+                const T yi = fmaT(-al, zn, wi);                     // y_i, eq. (4)
                 V.t[i] = ti;
                 V.p[i] = pn;
                 V.s[i] = sn;
                 V.z[i] = zn;
                 V.q[i] = qi;
                 V.y[i] = yi;
-                const double r0i = V.r0[i];
-                d1[0] = fma(qi, yi, d1[0]);
-                d1[1] = fma(yi, yi, d1[1]);
-                d1[2] = fma(qi, qi, d1[2]);
-                d1[3] = fma(r0i, sn, d1[3]);
-                d1[4] = fma(r0i, zn, d1[4]);
+                const double r0d = V.r0[i], qd = qi, yd = yi;
+                d1[0] = fma(qd, yd, d1[0]);
+                d1[1] = fma(yd, yd, d1[1]);
+                d1[2] = fma(qd, qd, d1[2]);
+                d1[3] = fma(r0d, (double)sn, d1[3]);
+                d1[4] = fma(r0d, (double)zn, d1[4]);
             }
             ++spmvs;
         } else {
             // replacement, second part: t_i = A w_i (w_i replaced), p_i; then s_i := A p_i; z_i := A s_i
             PBCG_ROWS(i) {
-                V.t[i] = A.row(i, VecLoad{V.w});
-                V.p[i] = fma(beta, fma(-omega, V.s[i], V.p[i]), V.r[i]);
+                V.t[i] = A.row(i, VecLoadT<T>{V.w});
+                V.p[i] = fmaT(be, fmaT(-om, V.s[i], V.p[i]), V.r[i]);
             }
             if (!grid_sync(g, sm, sflag)) return false;
-            PBCG_ROWS(i) { V.s[i] = A.row(i, VecLoad{V.p}); }
+            PBCG_ROWS(i) { V.s[i] = A.row(i, VecLoadT<T>{V.p}); }
             if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
-                const double zn = A.row(i, VecLoad{V.s});
-                const double sn = V.s[i], ri = V.r[i], wi = V.w[i];
-                const double qi = fma(-alpha, sn, ri);
-                const double yi = fma(-alpha, zn, wi);
+                const T zn = A.row(i, VecLoadT<T>{V.s});
+                const T sn = V.s[i], ri = V.r[i], wi = V.w[i];
+                const T qi = fmaT(-al, sn, ri);
+                const T yi = fmaT(-al, zn, wi);
                 V.z[i] = zn;
                 V.q[i] = qi;
                 V.y[i] = yi;
-                const double r0i = V.r0[i];
-                d1[0] = fma(qi, yi, d1[0]);
-                d1[1] = fma(yi, yi, d1[1]);
-                d1[2] = fma(qi, qi, d1[2]);
-                d1[3] = fma(r0i, sn, d1[3]);
-                d1[4] = fma(r0i, zn, d1[4]);
+                const double r0d = V.r0[i], qd = qi, yd = yi;
+                d1[0] = fma(qd, yd, d1[0]);
+                d1[1] = fma(yd, yd, d1[1]);
+                d1[2] = fma(qd, qd, d1[2]);
+                d1[3] = fma(r0d, (double)sn, d1[3]);
+                d1[4] = fma(r0d, (double)zn, d1[4]);
             }
             spmvs += 3;
         }
@@ -227,7 +236,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
         const bool small_q = !fixed && norm_below(qq, tol, tol2);
         if (small_q || yy == 0.0) {
             if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
-            PBCG_ROWS(i) { x[i] = fma(alpha, V.p[i], x[i]); }   // half step x_i + alpha_i p_i
+            PBCG_ROWS(i) { x[i] = fmaT(al, V.p[i], x[i]); }   // half step x_i + alpha_i p_i
             if (!grid_sync(g, sm, sflag)) return false;
             ++it;
             o.nr = qq;
@@ -243,35 +252,36 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgs &a, 
         const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
                                  (a.max_repl < 0 || o.nrr < a.max_repl);
         double d2[3] = {0.0, 0.0, 0.0};   // (r0,r) (r0,w) (r,r)
+        const T om2 = (T)omega;
         if (!replace_now) {
             PBCG_ROWS(i) {
-                const double vi = A.row(i, VecLoad{V.z});
-                const double qi = V.q[i], yi = V.y[i];
-                x[i] = fma(omega, qi, fma(alpha, V.p[i], x[i]));
-                const double rn = fma(-omega, yi, qi);                        // eq. (7)
-                const double wn = fma(-omega, fma(-alpha, vi, V.t[i]), yi);   // eq. (8)
+                const T vi = A.row(i, VecLoadT<T>{V.z});
+                const T qi = V.q[i], yi = V.y[i];
+                x[i] = fmaT(om2, qi, fmaT(al, V.p[i], x[i]));
+                const T rn = fmaT(-om2, yi, qi);                        // eq. (7)
+                const T wn = fmaT(-om2, fmaT(-al, vi, V.t[i]), yi);     // eq. (8)
                 V.v[i] = vi;
                 V.r[i] = rn;
                 V.w[i] = wn;
-                const double r0i = V.r0[i];
-                d2[0] = fma(r0i, rn, d2[0]);
-                d2[1] = fma(r0i, wn, d2[1]);
-                d2[2] = fma(rn, rn, d2[2]);
+                const double r0d = V.r0[i], rd = rn;
+                d2[0] = fma(r0d, rd, d2[0]);
+                d2[1] = fma(r0d, (double)wn, d2[1]);
+                d2[2] = fma(rd, rd, d2[2]);
             }
             ++spmvs;
         } else {
             // replacement, first part: x_{i+1}; r_{i+1} := b - A x_{i+1}; w_{i+1} := A r_{i+1}
-            PBCG_ROWS(i) { x[i] = fma(omega, V.q[i], fma(alpha, V.p[i], x[i])); }
+            PBCG_ROWS(i) { x[i] = fmaT(om2, V.q[i], fmaT(al, V.p[i], x[i])); }
             if (!grid_sync(g, sm, sflag)) return false;
-            PBCG_ROWS(i) { V.r[i] = a.b[i] - A.row(i, VecLoad{x}); }
+            PBCG_ROWS(i) { V.r[i] = a.b[i] - A.row(i, VecLoadT<T>{x}); }
             if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
-                const double wn = A.row(i, VecLoad{V.r});
-                const double rn = V.r[i], r0i = V.r0[i];
+                const T wn = A.row(i, VecLoadT<T>{V.r});
+                const double rd = V.r[i], r0d = V.r0[i];
                 V.w[i] = wn;
-                d2[0] = fma(r0i, rn, d2[0]);
-                d2[1] = fma(r0i, wn, d2[1]);
-                d2[2] = fma(rn, rn, d2[2]);
+                d2[0] = fma(r0d, rd, d2[0]);
+                d2[1] = fma(r0d, (double)wn, d2[1]);
+                d2[2] = fma(rd, rd, d2[2]);
             }
             spmvs += 2;
             o.nrr++;
@@ -306,7 +316,7 @@ __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(c
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
     Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
     int spmvs = 0;
-    if (!pipelined_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
+    if (!pipelined_loop<Op, double>(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
     finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
 }
 
@@ -458,6 +468,101 @@ __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(co
     int spmvs = 0;
     if (!standard_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
     finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+}
+
+// ===========================================================================
+// Mixed precision: FP64 iterative refinement around an FP32 pipelined solve.
+// Each refinement step computes the true residual r = b - A x with the FP64
+// matrix and FP64 vectors, rounds it to float, solves A d = r with Algorithm 9
+// on float vectors and the low-precision copy of A (FP32 or BF16 values; dot
+// products accumulated in FP64), and adds d to x in FP64. The true residual of
+// the last step is the reported one. The inner solve runs without residual
+// replacement: the FP64 residual of every refinement step plays that role.
+// ===========================================================================
+struct MixedArgs {
+    int n;
+    const double *b;
+    double *x;
+    float *d;            // correction of the current step (inner solution)
+    float *rhs;          // residual of the current step, rounded to float
+    VectorsT<float> V;   // inner work vectors
+    Control *ctl;
+    double *partials;
+    double *hist;        // nullable: true residual norm before each step, length max_outer + 1
+    double rtol;
+    int max_outer;
+    double inner_rtol;
+    int inner_maxit;
+};
+
+template <class Op64, class Op32>
+__global__ void __launch_bounds__(kTPB, 8) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ int sflag;
+    GridSync g{m.ctl, m.partials, 0u, 0};
+    const int lo = (int)((long long)blockIdx.x * m.n / gridDim.x);
+    const int hi = (int)((long long)(blockIdx.x + 1) * m.n / gridDim.x);
+    int outer = 0, inner_total = 0, status = PBCG_NOT_CONVERGED, spmvs = 0;
+    double nr0 = 0.0, tol = 0.0, tol2 = 0.0, last = 0.0;
+    for (;;) {
+        if (outer > 0) {
+            PBCG_ROWS(i) { m.x[i] = m.x[i] + (double)m.d[i]; }
+            if (!grid_sync(g, sm, &sflag)) return;
+        }
+        double d[1] = {0.0};
+        PBCG_ROWS(i) {
+            const double r = m.b[i] - A.row(i, VecLoad{m.x});
+            m.rhs[i] = (float)r;
+            m.d[i] = 0.0f;
+            d[0] = fma(r, r, d[0]);
+        }
+        ++spmvs;
+        if (!grid_sum<1>(g, d, sm, &sflag)) return;
+        last = d[0];
+        if (outer == 0) {
+            nr0 = sqrt(d[0]);
+            tol = __dmul_rn(m.rtol, nr0);
+            tol2 = __dmul_rn(tol, tol);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0 && m.hist) m.hist[outer] = d[0];
+        if (!isfinite(d[0])) { status = PBCG_NONFINITE; break; }
+        if (nr0 == 0.0 || norm_below(d[0], tol, tol2)) { status = PBCG_OK; break; }
+        if (outer >= m.max_outer) break;
+        SolveArgsT<float> ia;
+        ia.n = m.n;
+        ia.b = m.rhs;
+        ia.x = m.d;
+        ia.V = m.V;
+        ia.ctl = m.ctl;
+        ia.partials = m.partials;
+        ia.hist = nullptr;
+        ia.rtol = m.inner_rtol;
+        ia.limit = m.inner_maxit;
+        ia.fixed = 0;
+        ia.replace_period = 0;
+        ia.max_repl = -1;
+        ia.variant = 0;
+        Outcome io{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+        if (!pipelined_loop<Op32, float>(A32, ia, g, sm, &sflag, lo, hi, io, spmvs)) return;
+        inner_total += io.iters;
+        ++outer;
+        if (io.status == PBCG_NONFINITE) { status = PBCG_NONFINITE; break; }
+    }
+    if (blockIdx.x == 0) {
+        if (m.hist)
+            for (int i = (int)threadIdx.x; i <= outer; i += kTPB) m.hist[i] = sqrt(m.hist[i]);
+        if (threadIdx.x == 0) {
+            Control *c = m.ctl;
+            c->iters = outer;
+            c->inner_iters = inner_total;
+            c->status = status;
+            c->grid_syncs = g.count;
+            c->spmvs = spmvs;
+            c->nr0 = nr0;
+            c->rel_true = nr0 > 0.0 ? sqrt(last) / nr0 : sqrt(last);
+            c->rel_rec = c->rel_true;
+        }
+    }
 }
 
 // y = A x, one row per thread, grid-stride.

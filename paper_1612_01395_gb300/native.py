@@ -30,7 +30,9 @@ PBCG_PREC_NONE, PBCG_PREC_JACOBI = 0, 1
 # Exported symbols, as declared in include/pbicgstab.h.
 EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_create_csr", "pbicgstab_create_stencil",
            "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
-           "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc"]
+           "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
+           "pbicgstab_solve_mixed"]
+PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
 
@@ -57,6 +59,16 @@ class PbcgInfo(ctypes.Structure):
                 ("rel_res_recursive", ctypes.c_double), ("rel_res_true", ctypes.c_double),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("grid_syncs", ctypes.c_int32),
                 ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PbcgMixedInfo(ctypes.Structure):
+    _fields_ = [("outer", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("nr0", ctypes.c_double), ("rel_res_true", ctypes.c_double),
+                ("grid_syncs", ctypes.c_int32), ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
+                ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -105,6 +117,8 @@ def lib():
         L.pbicgstab_solve_host.argtypes = [vp, i32, vp, vp, f64, i32, i32, ctypes.POINTER(PbcgOpts),
                                            ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_spmv.argtypes = [vp, vp, vp]
+        L.pbicgstab_solve_mixed.argtypes = [vp, vp, i32, vp, vp, f64, i32, f64, i32, ctypes.POINTER(PbcgOpts),
+                                            ctypes.POINTER(PbcgMixedInfo)]
         L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
                                                   ctypes.POINTER(PbcgOpts), vp, ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_size.argtypes = [vp]
@@ -114,7 +128,8 @@ def lib():
         L.pbicgstab_last_error.argtypes = []
         L.pbicgstab_last_error.restype = ctypes.c_char_p
         for name in ("pbicgstab_create_csr", "pbicgstab_create_stencil", "pbicgstab_solve", "bicgstab_solve",
-                     "pbicgstab_solve_host", "pbicgstab_spmv", "pbicgstab_solve_csr_noalloc"):
+                     "pbicgstab_solve_host", "pbicgstab_spmv", "pbicgstab_solve_csr_noalloc",
+                     "pbicgstab_solve_mixed"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -191,6 +206,14 @@ def pbicgstab_solve_csr_noalloc(n, nnz, d_rowptr, d_col, d_val, d_b, d_x, rtol, 
     st = lib().pbicgstab_solve_csr_noalloc(int(n), int(nnz), d_rowptr, d_col, d_val, d_b, d_x, float(rtol),
                                            int(maxit), int(replace_period), ctypes.byref(o), stream,
                                            ctypes.byref(info))
+    return st, info
+
+
+def pbicgstab_solve_mixed(h, d_val_lowp, lowp_type, d_b, d_x, rtol, max_outer, inner_rtol, inner_maxit, **opts):
+    info = PbcgMixedInfo()
+    o = _opts(**opts)
+    st = lib().pbicgstab_solve_mixed(h, d_val_lowp, int(lowp_type), d_b, d_x, float(rtol), int(max_outer),
+                                     float(inner_rtol), int(inner_maxit), ctypes.byref(o), ctypes.byref(info))
     return st, info
 
 
@@ -306,6 +329,25 @@ class Solver:
         d = info.as_dict()
         if hist is not None:
             return x, d, hist[: d["iters"] + 1]
+        return x, d
+
+    def solve_mixed(self, b, values_lowp, lowp_type=PBCG_VALUES_F32, x0=None, rtol=1e-10, max_outer=30,
+                    inner_rtol=1e-4, inner_maxit=2000, history=False, **opts):
+        """FP64 refinement around FP32 Algorithm 9 (CSR handles); values_lowp is a
+        float32 or bfloat16 tensor with the CSR values. Returns (x, info[, history])."""
+        torch = self._torch()
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        hist = None
+        if history:
+            hist = torch.full((max_outer + 1,), float("nan"), dtype=torch.float64, device=b.device)
+            opts["d_history"] = hist.data_ptr()
+        st, info = pbicgstab_solve_mixed(self.h, values_lowp.data_ptr(), lowp_type, b.data_ptr(), x.data_ptr(),
+                                         rtol, max_outer, inner_rtol, inner_maxit, **opts)
+        if st in (PBCG_ERR_ARG, PBCG_ERR_CUDA, PBCG_ERR_OOM, PBCG_ERR_TIMEOUT):
+            raise PbcgError(st, pbicgstab_last_error())
+        d = info.as_dict()
+        if hist is not None:
+            return x, d, hist[: d["outer"] + 1]
         return x, d
 
     def close(self):

@@ -63,7 +63,7 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     fields = {
         "pbcg_coef": native.PbcgCoef, "pbcg_stencil": native.PbcgStencil,
-        "pbcg_opts": native.PbcgOpts, "pbcg_info": native.PbcgInfo,
+        "pbcg_opts": native.PbcgOpts, "pbcg_info": native.PbcgInfo, "pbcg_mixed_info": native.PbcgMixedInfo,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pbicgstab.h"', "int main(void){"]
     for cname, py in fields.items():

@@ -51,6 +51,8 @@ typedef enum {
                                limit; results are invalid, the context stays usable */
 } pbcg_status;
 
+/* Preconditioners (right preconditioning, Section 3.6): none, or Jacobi
+ * M = diag(A), applied elementwise inside the sweeps of Algorithms 10 and 11. */
 typedef enum { PBCG_PREC_NONE = 0, PBCG_PREC_JACOBI = 1 } pbcg_prec;
 
 /* One stencil coefficient as a function of the grid node (i, j, k):
@@ -122,13 +124,19 @@ typedef struct {
  * start required). Covers 12 FP64 vectors of length n and a control block. */
 size_t pbicgstab_workspace_bytes(int32_t n);
 
+/* Workspace of a handle created with PBCG_PREC_JACOBI: 6 more FP64 vectors
+ * (M^{-1} and the preconditioned vectors r^, s^, z^, q^, w^ of Algorithm 11). */
+size_t pbicgstab_workspace_bytes_prec(int32_t n);
+
 /* Create a handle for a CSR matrix (Section 3: A general sparse, unsymmetric).
  *   n, nnz         size; 0 <= n, 0 <= nnz < 2^31
  *   d_rowptr[n+1]  row offsets (d_rowptr[0] == 0, non-decreasing, d_rowptr[n] == nnz)
  *   d_col[nnz]     column indices in [0, n)
  *   d_val[nnz]     values
- *   prec           PBCG_PREC_NONE (PBCG_PREC_JACOBI returns PBCG_ERR_ARG: not built yet)
- *   d_workspace    caller-owned, >= pbicgstab_workspace_bytes(n) bytes, 256-byte aligned
+ *   prec           PBCG_PREC_NONE, or PBCG_PREC_JACOBI (M^{-1} = 1/diag(A) computed here;
+ *                  a zero or missing diagonal entry returns PBCG_ERR_ARG)
+ *   d_workspace    caller-owned, >= pbicgstab_workspace_bytes(n) bytes (PBCG_PREC_JACOBI:
+ *                  pbicgstab_workspace_bytes_prec(n)), 256-byte aligned
  *   stream         a cudaStream_t (NULL = legacy default stream)
  * The structure is validated on the device (one synchronisation); an invalid
  * matrix returns PBCG_ERR_ARG and no handle. */
@@ -141,7 +149,8 @@ pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr
 pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, void *d_workspace,
                                      size_t ws_bytes, void *stream, pbicgstab_t *out);
 
-/* Pipelined BiCGStab, Algorithm 9, with residual replacement (Section 4.2).
+/* Pipelined BiCGStab, Algorithm 9 (Algorithm 11 on a PBCG_PREC_JACOBI handle),
+ * with residual replacement (Section 4.2; preconditioned: r, r^, w, s, s^, z).
  *   d_b[n]           right-hand side
  *   d_x[n]           in: x_0; out: the last iterate
  *   rtol             stop when ||r_i||_2 <= rtol * ||r_0||_2 on the recursive residual
@@ -156,8 +165,9 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
 pbcg_status pbicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
                             int32_t replace_period, const pbcg_opts *opts, pbcg_info *info);
 
-/* Standard BiCGStab, Algorithm 7, on the same handle and workspace. Arguments
- * as pbicgstab_solve without replacement. */
+/* Standard BiCGStab, Algorithm 7 (Algorithm 10 on a PBCG_PREC_JACOBI handle,
+ * always in the five-exchange form), on the same handle and workspace.
+ * Arguments as pbicgstab_solve without replacement. */
 pbcg_status bicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
                            const pbcg_opts *opts, pbcg_info *info);
 
@@ -210,6 +220,49 @@ enum { PBCG_VALUES_F32 = 0, PBCG_VALUES_BF16 = 1 };
 pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lowp, int32_t lowp_type, const double *d_b,
                                   double *d_x, double rtol, int32_t max_outer, double inner_rtol,
                                   int32_t inner_maxit, const pbcg_opts *opts, pbcg_mixed_info *info);
+
+/* Batched solves: nsys independent CSR systems concatenated. System s owns
+ * rows [row_offset[s], row_offset[s+1]) of the concatenation; d_rowptr holds
+ * offsets into the shared d_col / d_val arrays (total nnz < 2^31); column
+ * indices are local to their system (0 <= col < n_s). */
+typedef struct {
+    int32_t nsys;
+    int32_t nnz;                   /* total stored entries (length of d_col and d_val) */
+    const int64_t *d_row_offset;   /* [nsys + 1], d_row_offset[0] == 0 */
+    const int32_t *d_rowptr;       /* [total rows + 1] */
+    const int32_t *d_col;
+    const double *d_val;
+} pbcg_batch;
+
+/* Per-system result of a batched solve (written to device memory). */
+typedef struct {
+    int32_t iters;
+    int32_t status;           /* pbcg_status; PBCG_ERR_ARG for an invalid system structure */
+    int32_t half_step;
+    int32_t n_replacements;
+    double rel_res_recursive;
+    double rel_res_true;
+} pbcg_batch_result;
+
+/* Workspace of a batched solve: 10 FP64 vectors over all rows + a counter. */
+size_t pbicgstab_batched_workspace_bytes(int64_t total_rows);
+
+/* Solve every system of the batch with pipelined BiCGStab (Algorithm 9 with
+ * residual replacement every replace_period iterations, 0 = off), each to
+ * ||r|| <= rtol ||r_0|| of its own, in one launch (an extension of the
+ * paper's method to many small systems; no counterpart in the paper).
+ * Each system is solved by one thread block with block-level reductions, so
+ * systems converge independently; blocks take systems in index order from a
+ * counter (order them largest first). Fully asynchronous on `stream`: no host
+ * synchronisation and no allocation, so a call can be captured into a CUDA
+ * graph and replayed. d_b, d_x (in: x0, out: x) span all rows; d_results
+ * receives nsys pbcg_batch_result in device memory; the workspace must stay
+ * untouched until the work completes. Column indices are checked on the
+ * device per system (an invalid system gets PBCG_ERR_ARG and is skipped).
+ * Host-side argument errors return PBCG_ERR_ARG immediately. */
+pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows, const double *d_b, double *d_x,
+                                    double rtol, int32_t maxit, int32_t replace_period, void *d_workspace,
+                                    size_t ws_bytes, pbcg_batch_result *d_results, void *stream);
 
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
 #define PBCG_NOALLOC_MAX_N 32768

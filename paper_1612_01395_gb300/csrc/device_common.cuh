@@ -214,4 +214,24 @@ __device__ __forceinline__ bool grid_sum(GridSync &g, double (&v)[K], double (*s
     return true;
 }
 
+// Synchronisation policy of a solve owned by one thread block (batched
+// solves): the "grid" is the block, a barrier is __syncthreads and a reduction
+// is the block sum. Same interface as GridSync, so the solver loops are shared.
+struct BlockSync {
+    int count;
+};
+
+__device__ __forceinline__ bool grid_sync(BlockSync &g, double (*)[32], int *) {
+    __syncthreads();
+    g.count++;
+    return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_sum(BlockSync &g, double (&v)[K], double (*sm)[32], int *) {
+    block_sum<K>(v, sm);   // its __syncthreads also orders the block's stores of the phase
+    g.count++;
+    return true;
+}
+
 }  // namespace pbcg

@@ -29,6 +29,7 @@ pbcg_status fail(pbcg_status st, const char *fmt, ...) {
 
 constexpr size_t kAlign = 256;
 constexpr int kVectors = 12;   // r r0 p s z q y w t v + host staging b, x
+constexpr int kPrecVectors = 6;   // preconditioned handles: M^{-1}, r^ s^ z^ q^ w^
 
 size_t vec_stride(int32_t n) { return ((size_t)(n > 0 ? n : 1) + 31) / 32 * 32; }   // doubles
 
@@ -48,6 +49,9 @@ struct pbicgstab_s {
     pbcg::Control *ctl;
     double *partials;
     cudaEvent_t ev0, ev1;   // bracket the solver kernel
+    int prec;               // pbcg_prec of the handle
+    int occ_pipe_prec, occ_plain_prec;
+    double *minv, *rh, *sh, *zh, *qh, *wh;   // Jacobi: M^{-1} and the hat vectors
 };
 
 extern "C" {
@@ -55,6 +59,11 @@ extern "C" {
 size_t pbicgstab_workspace_bytes(int32_t n) {
     if (n < 0) return 0;
     return pbcg::kControlBytes + pbcg::kPartialBytes + (size_t)kVectors * vec_stride(n) * sizeof(double);
+}
+
+size_t pbicgstab_workspace_bytes_prec(int32_t n) {
+    if (n < 0) return 0;
+    return pbicgstab_workspace_bytes(n) + (size_t)kPrecVectors * vec_stride(n) * sizeof(double);
 }
 
 const char *pbicgstab_last_error(void) { return g_err; }
@@ -67,19 +76,28 @@ namespace {
 
 template <class Op>
 pbcg_status occupancy(int *pipe, int *plain) {
-    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(pipe, pbcg::pbicgstab_kernel<Op>, pbcg::kTPB, 0));
-    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(plain, pbcg::bicgstab_kernel<Op>, pbcg::kTPB, 0));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(pipe, pbcg::pbicgstab_kernel<Op, false>, pbcg::kTPB, 0));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(plain, pbcg::bicgstab_kernel<Op, false>, pbcg::kTPB, 0));
+    if (*pipe < 1 || *plain < 1) return fail(PBCG_ERR_CUDA, "solver kernel cannot be resident on an SM");
+    return PBCG_OK;
+}
+
+template <class Op>
+pbcg_status occupancy_prec(int *pipe, int *plain) {
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(pipe, pbcg::pbicgstab_kernel<Op, true>, pbcg::kTPB, 0));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(plain, pbcg::bicgstab_kernel<Op, true>, pbcg::kTPB, 0));
     if (*pipe < 1 || *plain < 1) return fail(PBCG_ERR_CUDA, "solver kernel cannot be resident on an SM");
     return PBCG_OK;
 }
 
 pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, size_t ws_bytes, void *stream,
                         bool events = true) {
-    if (prec != PBCG_PREC_NONE)
-        return fail(PBCG_ERR_ARG, "preconditioner %d is not available (only PBCG_PREC_NONE)", (int)prec);
+    if (prec != PBCG_PREC_NONE && prec != PBCG_PREC_JACOBI)
+        return fail(PBCG_ERR_ARG, "unknown preconditioner %d", (int)prec);
     if (!d_ws) return fail(PBCG_ERR_ARG, "workspace is NULL");
     if (((uintptr_t)d_ws) % kAlign) return fail(PBCG_ERR_ARG, "workspace must be 256-byte aligned");
-    const size_t need = pbicgstab_workspace_bytes(n);
+    const size_t need = prec == PBCG_PREC_JACOBI ? pbicgstab_workspace_bytes_prec(n) : pbicgstab_workspace_bytes(n);
+    h->prec = (int)prec;
     if (ws_bytes < need) return fail(PBCG_ERR_OOM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
     h->n = n;
     h->ws = (char *)d_ws;
@@ -100,6 +118,27 @@ pbcg_status common_init(pbicgstab_s *h, int32_t n, pbcg_prec prec, void *d_ws, s
     double **slots[kVectors] = {&h->V.r, &h->V.r0, &h->V.p, &h->V.s, &h->V.z, &h->V.q,
                                 &h->V.y, &h->V.w, &h->V.t, &h->V.v, &h->b_stage, &h->x_stage};
     for (int k = 0; k < kVectors; ++k) *slots[k] = v0 + (size_t)k * s;
+    if (prec == PBCG_PREC_JACOBI) {
+        double **pslots[kPrecVectors] = {&h->minv, &h->rh, &h->sh, &h->zh, &h->qh, &h->wh};
+        for (int k = 0; k < kPrecVectors; ++k) *pslots[k] = v0 + (size_t)(kVectors + k) * s;
+    }
+    return PBCG_OK;
+}
+
+// M^{-1} = 1 / diag(A) into the workspace; a zero diagonal is an argument error.
+template <class Launch>
+pbcg_status setup_jacobi(pbicgstab_s *h, Launch launch) {
+    int *flag = &h->ctl->abort;
+    PBCG_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), h->stream));
+    int blocks = (h->n + 255) / 256;
+    if (blocks > 4 * h->num_sms) blocks = 4 * h->num_sms;
+    if (blocks < 1) blocks = 1;
+    launch(blocks, flag);
+    PBCG_CUDA(cudaGetLastError());
+    int bad = 0;
+    PBCG_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PBCG_CUDA(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(PBCG_ERR_ARG, "Jacobi preconditioner: a diagonal entry is zero or missing");
     return PBCG_OK;
 }
 
@@ -123,7 +162,10 @@ int pick_grid(const pbicgstab_s *h, int occ, int req) {
 template <class Op>
 pbcg_status launch_solver(pbicgstab_s *h, const Op &op, bool pipelined, const pbcg::SolveArgs &args, int grid) {
     void *params[2] = {(void *)&op, (void *)&args};
-    const void *fn = pipelined ? (const void *)pbcg::pbicgstab_kernel<Op> : (const void *)pbcg::bicgstab_kernel<Op>;
+    const void *fn = pipelined ? (args.minv ? (const void *)pbcg::pbicgstab_kernel<Op, true>
+                                            : (const void *)pbcg::pbicgstab_kernel<Op, false>)
+                               : (args.minv ? (const void *)pbcg::bicgstab_kernel<Op, true>
+                                            : (const void *)pbcg::bicgstab_kernel<Op, false>);
     PBCG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(pbcg::kTPB), params, 0, h->stream));
     return PBCG_OK;
 }
@@ -160,8 +202,16 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
     // 18 more FP64 operations per row; at ~1.9 FP64 FMA/clk/SM and ~1.4 us per
     // synchronisation the two break even near n = 1e5.
     a.variant = o.plain_variant ? o.plain_variant : (h->n < 100000 ? 3 : 5);
+    a.minv = h->prec == PBCG_PREC_JACOBI ? h->minv : nullptr;
+    a.rh = h->rh;
+    a.sh = h->sh;
+    a.zh = h->zh;
+    a.qh = h->qh;
+    a.wh = h->wh;
 
-    const int grid = pick_grid(h, pipelined ? h->occ_pipe : h->occ_plain, o.grid);
+    const int occ = h->prec == PBCG_PREC_JACOBI ? (pipelined ? h->occ_pipe_prec : h->occ_plain_prec)
+                                                : (pipelined ? h->occ_pipe : h->occ_plain);
+    const int grid = pick_grid(h, occ, o.grid);
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
     if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
     if (h->n > 0) {
@@ -239,8 +289,13 @@ pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr
         h->kind = 0;
         h->csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
         st = occupancy<pbcg::CsrOp>(&h->occ_pipe, &h->occ_plain);
+        if (st == PBCG_OK) st = occupancy_prec<pbcg::CsrOp>(&h->occ_pipe_prec, &h->occ_plain_prec);
     }
     if (st == PBCG_OK) st = check_csr(h, n, nnz, d_rowptr, d_col);
+    if (st == PBCG_OK && prec == PBCG_PREC_JACOBI && n > 0)
+        st = setup_jacobi(h, [&](int blocks, int *flag) {
+            pbcg::jacobi_csr_kernel<<<blocks, 256, 0, h->stream>>>(n, d_rowptr, d_col, d_val, h->minv, flag);
+        });
     if (st != PBCG_OK) {
         pbicgstab_destroy(h);
         return st;
@@ -298,7 +353,12 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
             o.c[d] = q;
         }
         st = occupancy<pbcg::StencilOp>(&h->occ_pipe, &h->occ_plain);
+        if (st == PBCG_OK) st = occupancy_prec<pbcg::StencilOp>(&h->occ_pipe_prec, &h->occ_plain_prec);
     }
+    if (st == PBCG_OK && prec == PBCG_PREC_JACOBI)
+        st = setup_jacobi(h, [&](int blocks, int *flag) {
+            pbcg::jacobi_stencil_kernel<<<blocks, 256, 0, h->stream>>>(h->st, h->minv, flag);
+        });
     if (st != PBCG_OK) {
         pbicgstab_destroy(h);
         return st;
@@ -454,6 +514,63 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
         if (h->ev0 && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) info->kernel_ms = ms;
     }
     return st;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves.
+// ---------------------------------------------------------------------------
+extern "C" size_t pbicgstab_batched_workspace_bytes(int64_t total_rows) {
+    if (total_rows < 0) return 0;
+    const size_t s = ((size_t)(total_rows > 0 ? total_rows : 1) + 31) / 32 * 32;
+    return 256 + 10 * s * sizeof(double);
+}
+
+extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows, const double *d_b,
+                                               double *d_x, double rtol, int32_t maxit, int32_t replace_period,
+                                               void *d_workspace, size_t ws_bytes, pbcg_batch_result *d_results,
+                                               void *stream) {
+    if (!batch) return fail(PBCG_ERR_ARG, "batch is NULL");
+    if (batch->nsys < 0 || batch->nnz < 0 || total_rows < 0) return fail(PBCG_ERR_ARG, "negative size");
+    if (batch->nsys == 0) return PBCG_OK;
+    if (!batch->d_row_offset || !batch->d_rowptr || !d_results) return fail(PBCG_ERR_ARG, "batch array is NULL");
+    if (batch->nnz > 0 && (!batch->d_col || !batch->d_val)) return fail(PBCG_ERR_ARG, "batch array is NULL");
+    if (total_rows > 0 && (!d_b || !d_x)) return fail(PBCG_ERR_ARG, "b or x is NULL");
+    if (!(rtol >= 0.0) || maxit < 0 || replace_period < 0) return fail(PBCG_ERR_ARG, "invalid tolerance or counts");
+    if (!d_workspace || ((uintptr_t)d_workspace) % kAlign) return fail(PBCG_ERR_ARG, "workspace NULL or unaligned");
+    if (ws_bytes < pbicgstab_batched_workspace_bytes(total_rows))
+        return fail(PBCG_ERR_OOM, "workspace has %zu bytes, needs %zu", ws_bytes,
+                    pbicgstab_batched_workspace_bytes(total_rows));
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0, occ = 0;
+    PBCG_CUDA(cudaGetDevice(&dev));
+    PBCG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::batched_kernel, pbcg::kTPB, 0));
+    if (occ < 1) return fail(PBCG_ERR_CUDA, "batched kernel cannot be resident on an SM");
+    pbcg::BatchArgs B;
+    B.nsys = batch->nsys;
+    B.nnz = batch->nnz;
+    B.total_rows = total_rows;
+    B.row_offset = (const long long *)batch->d_row_offset;
+    B.rowptr = batch->d_rowptr;
+    B.col = batch->d_col;
+    B.val = batch->d_val;
+    B.b = d_b;
+    B.x = d_x;
+    B.next = (unsigned *)d_workspace;
+    double *v0 = (double *)((char *)d_workspace + 256);
+    const size_t s = ((size_t)(total_rows > 0 ? total_rows : 1) + 31) / 32 * 32;
+    double **slots[10] = {&B.V.r, &B.V.r0, &B.V.p, &B.V.s, &B.V.z, &B.V.q, &B.V.y, &B.V.w, &B.V.t, &B.V.v};
+    for (int k = 0; k < 10; ++k) *slots[k] = v0 + (size_t)k * s;
+    B.out = d_results;
+    B.rtol = rtol;
+    B.maxit = maxit;
+    B.replace_period = replace_period;
+    int grid = occ * sms;
+    if (grid > batch->nsys) grid = batch->nsys;
+    PBCG_CUDA(cudaMemsetAsync(B.next, 0, sizeof(unsigned), st));
+    pbcg::batched_kernel<<<grid, pbcg::kTPB, 0, st>>>(B);
+    PBCG_CUDA(cudaGetLastError());
+    return PBCG_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -42,6 +42,10 @@ struct SolveArgsT {
     int replace_period;
     int max_repl;       // < 0: unlimited
     int variant;        // Algorithm 7 only: 3 or 5
+    // preconditioned solves (Algorithms 10 and 11): M^{-1} u = minv .* u and the
+    // hat vectors r^, s^, z^, q^, w^ (null when unpreconditioned)
+    const T *minv;
+    T *rh, *sh, *zh, *qh, *wh;
 };
 using SolveArgs = SolveArgsT<double>;
 
@@ -134,8 +138,8 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
 // float for the inner solves of the mixed-precision refinement. Dot products
 // are always accumulated in double, and alpha, beta, omega, rho are doubles;
 // a sweep uses them rounded to T.
-template <class Op, typename T>
-__device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> &a, GridSync &g, double (*sm)[32],
+template <class Op, typename T, class Sync = GridSync>
+__device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> &a, Sync &g, double (*sm)[32],
                                                int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
     const VectorsT<T> &V = a.V;
     T *x = a.x;
@@ -307,7 +311,211 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     return true;
 }
 
+// ===========================================================================
+// Algorithm 11 (preconditioned pipelined BiCGStab) with a diagonal M^{-1},
+// applied elementwise inside the sweeps, so an iteration still takes two
+// grid-wide exchanges: phase A forms z^ = M^{-1} z next to z, phase B forms
+// w^ = M^{-1} w next to w, and each SpMV reads the hat vector the previous
+// phase wrote (t = A w^, v = A z^). Residual replacement (Section 4.2) as in
+// the unpreconditioned loop: r := b - A x, r^ := M^{-1} r, w := A r^ before the
+// second reduction of iteration i-1; s := A p^, s^ := M^{-1} s, z := A s^
+// after p^_i. V.p holds p^.
+// ===========================================================================
 template <class Op>
+__device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+                                                    int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
+    const Vectors &V = a.V;
+    double *x = a.x;
+    const double *mi = a.minv;
+    double *rh = a.rh, *sh = a.sh, *zh = a.zh, *qh = a.qh, *wh = a.wh;
+    const bool fixed = a.fixed != 0;
+
+    // r_0 := b - A x_0; r0 := r_0; r^_0 := M^{-1} r_0; p^, s, s^, z, z^, v := 0
+    double d0[1] = {0.0};
+    PBCG_ROWS(i) {
+        const double ri = a.b[i] - A.row(i, VecLoad{x});
+        V.r[i] = ri;
+        V.r0[i] = ri;
+        rh[i] = mi[i] * ri;
+        V.p[i] = 0.0;
+        V.s[i] = 0.0;
+        sh[i] = 0.0;
+        V.z[i] = 0.0;
+        zh[i] = 0.0;
+        V.v[i] = 0.0;
+        d0[0] = fma(ri, ri, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    double rho = d0[0];
+    o.nr0 = sqrt(rho);
+    o.nr = o.nr0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
+    const double tol = __dmul_rn(a.rtol, o.nr0), tol2 = __dmul_rn(tol, tol);
+    if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
+
+    // w_0 := A r^_0; w^_0 := M^{-1} w_0; alpha_0 := (r0, r0) / (r0, w0)
+    d0[0] = 0.0;
+    PBCG_ROWS(i) {
+        const double wi = A.row(i, VecLoad{rh});
+        V.w[i] = wi;
+        wh[i] = mi[i] * wi;
+        d0[0] = fma(V.r0[i], wi, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    if (!isfinite(d0[0])) { o.status = PBCG_NONFINITE; return true; }
+    if (d0[0] == 0.0) { o.status = PBCG_BREAKDOWN; return true; }
+    double alpha = __ddiv_rn(rho, d0[0]), beta = 0.0, omega = 0.0;
+
+    bool replaced = false;
+    int it = 0;
+    while (it < a.limit) {
+        // ---- phase A: t = A w^; p^, s, s^, z, q, q^, y, z^; first reduction
+        double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
+        if (!replaced) {
+            PBCG_ROWS(i) {
+                const double ti = A.row(i, VecLoad{wh});
+                const double si = V.s[i], zi = V.z[i], shi = sh[i];
+                const double ph = fma(beta, fma(-omega, shi, V.p[i]), rh[i]);   // p^_i
+                const double sn = fma(beta, fma(-omega, zi, si), V.w[i]);       // s_i
+                const double shn = fma(beta, fma(-omega, zh[i], shi), wh[i]);   // s^_i
+                const double zn = fma(beta, fma(-omega, V.v[i], zi), ti);       // z_i
+                const double qi = fma(-alpha, sn, V.r[i]);                      // q_i
+                const double qhi = fma(-alpha, shn, rh[i]);                     // q^_i
+                const double yi = fma(-alpha, zn, V.w[i]);                      // y_i
+                V.t[i] = ti;
+                V.p[i] = ph;
+                V.s[i] = sn;
+                sh[i] = shn;
+                V.z[i] = zn;
+                zh[i] = mi[i] * zn;                                             // z^_i
+                V.q[i] = qi;
+                qh[i] = qhi;
+                V.y[i] = yi;
+                const double r0i = V.r0[i];
+                d1[0] = fma(qi, yi, d1[0]);
+                d1[1] = fma(yi, yi, d1[1]);
+                d1[2] = fma(qi, qi, d1[2]);
+                d1[3] = fma(r0i, sn, d1[3]);
+                d1[4] = fma(r0i, zn, d1[4]);
+            }
+            ++spmvs;
+        } else {
+            PBCG_ROWS(i) {
+                V.t[i] = A.row(i, VecLoad{wh});
+                V.p[i] = fma(beta, fma(-omega, sh[i], V.p[i]), rh[i]);
+            }
+            if (!grid_sync(g, sm, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double sn = A.row(i, VecLoad{V.p});
+                V.s[i] = sn;
+                sh[i] = mi[i] * sn;
+            }
+            if (!grid_sync(g, sm, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double zn = A.row(i, VecLoad{sh});
+                const double sn = V.s[i];
+                const double qi = fma(-alpha, sn, V.r[i]);
+                const double qhi = fma(-alpha, sh[i], rh[i]);
+                const double yi = fma(-alpha, zn, V.w[i]);
+                V.z[i] = zn;
+                zh[i] = mi[i] * zn;
+                V.q[i] = qi;
+                qh[i] = qhi;
+                V.y[i] = yi;
+                const double r0i = V.r0[i];
+                d1[0] = fma(qi, yi, d1[0]);
+                d1[1] = fma(yi, yi, d1[1]);
+                d1[2] = fma(qi, qi, d1[2]);
+                d1[3] = fma(r0i, sn, d1[3]);
+                d1[4] = fma(r0i, zn, d1[4]);
+            }
+            spmvs += 3;
+        }
+        if (!grid_sum<5>(g, d1, sm, sflag)) return false;
+        const double qy = d1[0], yy = d1[1], qq = d1[2], r0s = d1[3], r0z = d1[4];
+        if (!all_finite(d1)) { o.status = PBCG_NONFINITE; break; }
+        const bool small_q = !fixed && norm_below(qq, tol, tol2);
+        if (small_q || yy == 0.0) {
+            if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
+            PBCG_ROWS(i) { x[i] = fma(alpha, V.p[i], x[i]); }   // half step x_i + alpha_i p^_i
+            if (!grid_sync(g, sm, sflag)) return false;
+            ++it;
+            o.nr = qq;
+            o.half = 1;
+            o.status = PBCG_OK;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
+            break;
+        }
+        omega = __ddiv_rn(qy, yy);
+        if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+
+        // ---- phase B: v = A z^; x, r, r^, w, w^; second reduction
+        const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
+                                 (a.max_repl < 0 || o.nrr < a.max_repl);
+        double d2[3] = {0.0, 0.0, 0.0};   // (r0,r) (r0,w) (r,r)
+        if (!replace_now) {
+            PBCG_ROWS(i) {
+                const double vi = A.row(i, VecLoad{zh});
+                const double qi = V.q[i], yi = V.y[i];
+                x[i] = fma(omega, qh[i], fma(alpha, V.p[i], x[i]));
+                const double rn = fma(-omega, yi, qi);
+                const double rhn = fma(-omega, fma(-alpha, zh[i], wh[i]), qh[i]);
+                const double wn = fma(-omega, fma(-alpha, vi, V.t[i]), yi);
+                V.v[i] = vi;
+                V.r[i] = rn;
+                rh[i] = rhn;
+                V.w[i] = wn;
+                wh[i] = mi[i] * wn;
+                const double r0i = V.r0[i];
+                d2[0] = fma(r0i, rn, d2[0]);
+                d2[1] = fma(r0i, wn, d2[1]);
+                d2[2] = fma(rn, rn, d2[2]);
+            }
+            ++spmvs;
+        } else {
+            PBCG_ROWS(i) { x[i] = fma(omega, qh[i], fma(alpha, V.p[i], x[i])); }
+            if (!grid_sync(g, sm, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double rn = a.b[i] - A.row(i, VecLoad{x});
+                V.r[i] = rn;
+                rh[i] = mi[i] * rn;
+            }
+            if (!grid_sync(g, sm, sflag)) return false;
+            PBCG_ROWS(i) {
+                const double wn = A.row(i, VecLoad{rh});
+                const double rn = V.r[i], r0i = V.r0[i];
+                V.w[i] = wn;
+                wh[i] = mi[i] * wn;
+                d2[0] = fma(r0i, rn, d2[0]);
+                d2[1] = fma(r0i, wn, d2[1]);
+                d2[2] = fma(rn, rn, d2[2]);
+            }
+            spmvs += 2;
+            o.nrr++;
+        }
+        replaced = replace_now;
+        if (!grid_sum<3>(g, d2, sm, sflag)) return false;
+        ++it;
+        const double rho_n = d2[0], r0w = d2[1];
+        o.nr = d2[2];
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = d2[2];
+        if (!all_finite(d2)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && norm_below(d2[2], tol, tol2)) { o.status = PBCG_OK; break; }
+        if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
+        const double den = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
+        if (den == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        alpha = __ddiv_rn(rho_n, den);
+        rho = rho_n;
+    }
+    o.iters = it;
+    if (it == a.limit && o.status == PBCG_NOT_CONVERGED && fixed) o.status = PBCG_OK;
+    return true;
+}
+
+template <class Op, bool Prec>
 __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
@@ -316,7 +524,12 @@ __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(c
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
     Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
     int spmvs = 0;
-    if (!pipelined_loop<Op, double>(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
+    bool ok;
+    if constexpr (Prec)
+        ok = pipelined_prec_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    else
+        ok = pipelined_loop<Op, double>(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    if (!ok) return;
     finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
 }
 
@@ -457,7 +670,119 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, G
     return true;
 }
 
+// ===========================================================================
+// Algorithm 10 (preconditioned BiCGStab) with a diagonal M^{-1}: the
+// five-exchange form of the standard loop with p^ = M^{-1} p and
+// q^ = M^{-1} q written next to p and q. Buffers: V.z holds p^, a.qh holds q^.
+// ===========================================================================
 template <class Op>
+__device__ __forceinline__ bool standard_prec_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+                                                   int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
+    const Vectors &V = a.V;
+    double *x = a.x;
+    const double *mi = a.minv;
+    double *ph = V.z, *qh = a.qh;
+    const bool fixed = a.fixed != 0;
+
+    double d0[1] = {0.0};
+    PBCG_ROWS(i) {
+        const double ri = a.b[i] - A.row(i, VecLoad{x});
+        V.r[i] = ri;
+        V.r0[i] = ri;
+        V.p[i] = 0.0;
+        V.s[i] = 0.0;
+        d0[0] = fma(ri, ri, d0[0]);
+    }
+    ++spmvs;
+    if (!grid_sum<1>(g, d0, sm, sflag)) return false;
+    double rho = d0[0];
+    o.nr0 = sqrt(rho);
+    o.nr = o.nr0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
+    const double tol = __dmul_rn(a.rtol, o.nr0), tol2 = __dmul_rn(tol, tol);
+    if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
+    double beta = 0.0, omega = 0.0;
+
+    int it = 0;
+    while (it < a.limit) {
+        // p_i := r_i + beta (p_{i-1} - omega s_{i-1}); p^_i := M^{-1} p_i; s_i := A p^_i
+        PBCG_ROWS(i) {
+            const double pn = fma(beta, fma(-omega, V.s[i], V.p[i]), V.r[i]);
+            V.p[i] = pn;
+            ph[i] = mi[i] * pn;
+        }
+        if (!grid_sync(g, sm, sflag)) return false;
+        double d1[1] = {0.0};
+        PBCG_ROWS(i) {
+            const double si = A.row(i, VecLoad{ph});
+            V.s[i] = si;
+            d1[0] = fma(V.r0[i], si, d1[0]);
+        }
+        ++spmvs;
+        if (!grid_sum<1>(g, d1, sm, sflag)) return false;
+        if (!isfinite(d1[0])) { o.status = PBCG_NONFINITE; break; }
+        if (d1[0] == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        const double alpha = __ddiv_rn(rho, d1[0]);
+        // q_i := r_i - alpha s_i; q^_i := M^{-1} q_i; y_i := A q^_i
+        PBCG_ROWS(i) {
+            const double qi = fma(-alpha, V.s[i], V.r[i]);
+            V.q[i] = qi;
+            qh[i] = mi[i] * qi;
+        }
+        if (!grid_sync(g, sm, sflag)) return false;
+        double d2[3] = {0.0, 0.0, 0.0};
+        PBCG_ROWS(i) {
+            const double yi = A.row(i, VecLoad{qh});
+            const double qi = V.q[i];
+            V.y[i] = yi;
+            d2[0] = fma(qi, yi, d2[0]);
+            d2[1] = fma(yi, yi, d2[1]);
+            d2[2] = fma(qi, qi, d2[2]);
+        }
+        ++spmvs;
+        if (!grid_sum<3>(g, d2, sm, sflag)) return false;
+        const double qy = d2[0], yy = d2[1], qq = d2[2];
+        if (!all_finite(d2)) { o.status = PBCG_NONFINITE; break; }
+        const bool small_q = !fixed && norm_below(qq, tol, tol2);
+        if (small_q || yy == 0.0) {
+            if (!small_q && qq != 0.0) { o.status = PBCG_BREAKDOWN; break; }
+            PBCG_ROWS(i) { x[i] = fma(alpha, ph[i], x[i]); }
+            if (!grid_sync(g, sm, sflag)) return false;
+            ++it;
+            o.nr = qq;
+            o.half = 1;
+            o.status = PBCG_OK;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
+            break;
+        }
+        omega = __ddiv_rn(qy, yy);
+        if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        // x_{i+1} := x_i + alpha p^_i + omega q^_i; r_{i+1} := q_i - omega y_i
+        double d3[2] = {0.0, 0.0};
+        PBCG_ROWS(i) {
+            x[i] = fma(omega, qh[i], fma(alpha, ph[i], x[i]));
+            const double rn = fma(-omega, V.y[i], V.q[i]);
+            V.r[i] = rn;
+            d3[0] = fma(V.r0[i], rn, d3[0]);
+            d3[1] = fma(rn, rn, d3[1]);
+        }
+        if (!grid_sum<2>(g, d3, sm, sflag)) return false;
+        ++it;
+        const double rho_n = d3[0];
+        o.nr = d3[1];
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = d3[1];
+        if (!all_finite(d3)) { o.status = PBCG_NONFINITE; break; }
+        if (!fixed && norm_below(d3[1], tol, tol2)) { o.status = PBCG_OK; break; }
+        if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
+        beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
+        rho = rho_n;
+    }
+    o.iters = it;
+    if (it == a.limit && o.status == PBCG_NOT_CONVERGED && fixed) o.status = PBCG_OK;
+    return true;
+}
+
+template <class Op, bool Prec>
 __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
@@ -466,7 +791,12 @@ __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(co
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
     Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
     int spmvs = 0;
-    if (!standard_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs)) return;
+    bool ok;
+    if constexpr (Prec)
+        ok = standard_prec_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    else
+        ok = standard_loop(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    if (!ok) return;
     finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
 }
 
@@ -562,6 +892,125 @@ __global__ void __launch_bounds__(kTPB, 8) mixed_kernel(const Op64 A, const Op32
             c->rel_true = nr0 > 0.0 ? sqrt(last) / nr0 : sqrt(last);
             c->rel_rec = c->rel_true;
         }
+    }
+}
+
+// M^{-1} = 1 / diag(A) (Jacobi). A zero or non-finite diagonal entry sets *bad.
+__global__ void jacobi_csr_kernel(int n, const int *rowptr, const int *col, const double *val, double *minv, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double d = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (col[k] == i) d = val[k];
+        const double m = 1.0 / d;
+        if (d == 0.0 || !isfinite(m)) atomicOr(bad, 1);
+        minv[i] = m;
+    }
+}
+__global__ void jacobi_stencil_kernel(const StencilOp A, double *minv, int *bad) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < A.n; r += gridDim.x * blockDim.x) {
+        const int t = (int)A.dx.div((uint32_t)r);
+        const int i = r - t * A.nx;
+        const int k = (int)A.dy.div((uint32_t)t);
+        const int j = t - k * A.ny;
+        const double d = A.coef(PBCG_C, i, j, k);
+        const double m = 1.0 / d;
+        if (d == 0.0 || !isfinite(m)) atomicOr(bad, 1);
+        minv[r] = m;
+    }
+}
+
+// ===========================================================================
+// Batched solves: many independent systems in one launch. Each block takes the
+// next system from an atomic counter and solves it alone with Algorithm 9
+// (block-level reductions and barriers, BlockSync), so systems converge
+// independently and blocks never wait on each other -- no co-residency is
+// needed and the launch can be captured in a CUDA graph. System s owns the
+// global rows [row_offset[s], row_offset[s+1]) of the concatenated CSR arrays
+// (row pointers index the shared col/val arrays; column indices are local to
+// the system) and of b, x and the work vectors. Systems are taken in index
+// order; ordering them largest first balances the load.
+// ===========================================================================
+struct BatchArgs {
+    int nsys;
+    int nnz;
+    long long total_rows;
+    const long long *row_offset;   // [nsys + 1]
+    const int *rowptr;             // [total rows + 1], global offsets into col/val
+    const int *col;                // local column indices
+    const double *val;
+    const double *b;
+    double *x;
+    Vectors V;                     // global work vectors (total rows each)
+    unsigned *next;                // work counter, zero before the launch
+    pbcg_batch_result *out;        // [nsys]
+    double rtol;
+    int maxit;
+    int replace_period;
+};
+
+__global__ void __launch_bounds__(kTPB) batched_kernel(const BatchArgs B) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ int sflag;
+    __shared__ int s_sys;
+    for (;;) {
+        if (threadIdx.x == 0) s_sys = (int)atomicAdd(B.next, 1u);
+        __syncthreads();
+        const int sys = s_sys;
+        __syncthreads();
+        if (sys >= B.nsys) return;
+        const long long r0 = B.row_offset[sys], r1 = B.row_offset[sys + 1];
+        // structure check of this system: its rows inside the batch, entries inside
+        // the shared arrays, columns local to the system
+        int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
+        const int n = bad ? 0 : (int)(r1 - r0);
+        const CsrOp A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
+        for (int i = threadIdx.x; i < n; i += kTPB) {
+            const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
+            if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
+            for (int k = e0; k < e1 && !bad; ++k)
+                if (B.col[k] < 0 || B.col[k] >= n) bad = 1;
+        }
+        bad = __syncthreads_or(bad);
+        pbcg_batch_result res{0, PBCG_ERR_ARG, 0, 0, 0.0, 0.0};
+        if (!bad) {
+            SolveArgs a;
+            a.n = n;
+            a.b = B.b + r0;
+            a.x = B.x + r0;
+            a.V = Vectors{B.V.r + r0, B.V.r0 + r0, B.V.p + r0, B.V.s + r0, B.V.z + r0,
+                          B.V.q + r0, B.V.y + r0, B.V.w + r0, B.V.t + r0, B.V.v + r0};
+            a.ctl = nullptr;
+            a.partials = nullptr;
+            a.hist = nullptr;
+            a.rtol = B.rtol;
+            a.limit = B.maxit;
+            a.fixed = 0;
+            a.replace_period = B.replace_period;
+            a.max_repl = -1;
+            a.variant = 0;
+            a.minv = nullptr;
+            a.rh = a.sh = a.zh = a.qh = a.wh = nullptr;
+            BlockSync bs{0};
+            Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+            int spmvs = 0;
+            pipelined_loop<CsrOp, double, BlockSync>(A, a, bs, sm, &sflag, 0, n, o, spmvs);
+            // true residual of the returned x
+            double d[1] = {0.0};
+            for (int i = threadIdx.x; i < n; i += kTPB) {
+                const double rr = a.b[i] - A.row(i, VecLoad{a.x});
+                d[0] = fma(rr, rr, d[0]);
+            }
+            block_sum<1>(d, sm);
+            res.iters = o.iters;
+            res.status = o.status;
+            res.half_step = o.half;
+            res.n_replacements = o.nrr;
+            const double nr = o.iters > 0 ? sqrt(o.nr) : o.nr0;
+            res.rel_res_recursive = o.nr0 > 0.0 ? nr / o.nr0 : 0.0;
+            res.rel_res_true = o.nr0 > 0.0 ? sqrt(d[0]) / o.nr0 : sqrt(d[0]);
+        }
+        if (threadIdx.x == 0) B.out[sys] = res;
+        __syncthreads();
     }
 }
 

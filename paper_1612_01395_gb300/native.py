@@ -28,10 +28,10 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NONFINITE", 4: 
 PBCG_PREC_NONE, PBCG_PREC_JACOBI = 0, 1
 
 # Exported symbols, as declared in include/pbicgstab.h.
-EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_create_csr", "pbicgstab_create_stencil",
+EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_workspace_bytes_prec", "pbicgstab_create_csr", "pbicgstab_create_stencil",
            "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
            "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
-           "pbicgstab_solve_mixed"]
+           "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched"]
 PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
@@ -74,6 +74,17 @@ class PbcgMixedInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PbcgBatch(ctypes.Structure):
+    _fields_ = [("nsys", ctypes.c_int32), ("nnz", ctypes.c_int32), ("d_row_offset", ctypes.c_void_p),
+                ("d_rowptr", ctypes.c_void_p), ("d_col", ctypes.c_void_p), ("d_val", ctypes.c_void_p)]
+
+
+class PbcgBatchResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("half_step", ctypes.c_int32),
+                ("n_replacements", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double)]
+
+
 def sources():
     return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC)) if f.endswith((".cu", ".cuh"))] + \
         [os.path.join(_INCLUDE, "pbicgstab.h")]
@@ -109,6 +120,8 @@ def lib():
         vp, i32, f64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
         L.pbicgstab_workspace_bytes.argtypes = [i32]
         L.pbicgstab_workspace_bytes.restype = sz
+        L.pbicgstab_workspace_bytes_prec.argtypes = [i32]
+        L.pbicgstab_workspace_bytes_prec.restype = sz
         L.pbicgstab_create_csr.argtypes = [i32, i32, vp, vp, vp, ctypes.c_int, vp, sz, vp, ctypes.POINTER(vp)]
         L.pbicgstab_create_stencil.argtypes = [ctypes.POINTER(PbcgStencil), ctypes.c_int, vp, sz, vp,
                                                ctypes.POINTER(vp)]
@@ -119,6 +132,11 @@ def lib():
         L.pbicgstab_spmv.argtypes = [vp, vp, vp]
         L.pbicgstab_solve_mixed.argtypes = [vp, vp, i32, vp, vp, f64, i32, f64, i32, ctypes.POINTER(PbcgOpts),
                                             ctypes.POINTER(PbcgMixedInfo)]
+        L.pbicgstab_batched_workspace_bytes.argtypes = [ctypes.c_int64]
+        L.pbicgstab_batched_workspace_bytes.restype = sz
+        L.pbicgstab_solve_batched.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32, vp,
+                                              sz, vp, vp]
+        L.pbicgstab_solve_batched.restype = ctypes.c_int
         L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
                                                   ctypes.POINTER(PbcgOpts), vp, ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_size.argtypes = [vp]
@@ -149,6 +167,10 @@ def _opts(max_replacements=-1, fixed_iters=0, d_history=None, plain_variant=0, g
 
 def pbicgstab_workspace_bytes(n: int) -> int:
     return int(lib().pbicgstab_workspace_bytes(int(n)))
+
+
+def pbicgstab_workspace_bytes_prec(n: int) -> int:
+    return int(lib().pbicgstab_workspace_bytes_prec(int(n)))
 
 
 def pbicgstab_last_error() -> str:
@@ -217,6 +239,60 @@ def pbicgstab_solve_mixed(h, d_val_lowp, lowp_type, d_b, d_x, rtol, max_outer, i
     return st, info
 
 
+def pbicgstab_batched_workspace_bytes(total_rows: int) -> int:
+    return int(lib().pbicgstab_batched_workspace_bytes(int(total_rows)))
+
+
+def pbicgstab_solve_batched(batch: PbcgBatch, total_rows, d_b, d_x, rtol, maxit, replace_period, d_ws, ws_bytes,
+                            d_results, stream) -> int:
+    return lib().pbicgstab_solve_batched(ctypes.byref(batch), int(total_rows), d_b, d_x, float(rtol), int(maxit),
+                                         int(replace_period), d_ws, int(ws_bytes), d_results, stream)
+
+
+class BatchSolver:
+    """Device copies of a problems.Batch plus workspace and per-system results."""
+
+    RESULT_DTYPE = None
+
+    def __init__(self, batch):
+        import torch
+        import numpy as np
+        self.torch = torch
+        self.total = batch.total_rows
+        self.nsys = batch.nsys
+        self.row_offset = torch.as_tensor(batch.row_offset, dtype=torch.int64).cuda()
+        self.rowptr = torch.as_tensor(batch.rowptr, dtype=torch.int32).cuda()
+        self.col = torch.as_tensor(batch.col, dtype=torch.int32).cuda()
+        self.val = torch.as_tensor(batch.val, dtype=torch.float64).cuda()
+        nb = pbicgstab_batched_workspace_bytes(self.total)
+        self.ws = torch.empty(nb // 8 + 64, dtype=torch.float64, device="cuda")
+        self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.ws_bytes = nb
+        self.results = torch.zeros(self.nsys * ctypes.sizeof(PbcgBatchResult) // 8, dtype=torch.float64,
+                                   device="cuda")
+        self.desc = PbcgBatch(self.nsys, int(batch.rowptr[-1]), self.row_offset.data_ptr(), self.rowptr.data_ptr(),
+                              self.col.data_ptr(), self.val.data_ptr())
+        self._np = np
+
+    def launch(self, b, x, rtol=1e-8, maxit=1000, replace_period=0, stream=None):
+        """Enqueue the batched solve (asynchronous)."""
+        torch = self.torch
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        rc = pbicgstab_solve_batched(self.desc, self.total, b.data_ptr(), x.data_ptr(), rtol, maxit, replace_period,
+                                     self.ws_ptr, self.ws_bytes, self.results.data_ptr(), st)
+        if rc != PBCG_OK:
+            raise PbcgError(rc, pbicgstab_last_error())
+
+    def fetch_results(self):
+        """Per-system results as a numpy structured array (synchronises)."""
+        np = self._np
+        raw = self.results.cpu().numpy().tobytes()
+        dt = np.dtype([("iters", np.int32), ("status", np.int32), ("half_step", np.int32),
+                       ("n_replacements", np.int32), ("rel_res_recursive", np.float64),
+                       ("rel_res_true", np.float64)])
+        return np.frombuffer(raw, dtype=dt, count=self.nsys)
+
+
 def pbicgstab_spmv(h, d_x, d_y) -> int:
     return lib().pbicgstab_spmv(h, d_x, d_y)
 
@@ -249,9 +325,9 @@ class Solver:
             raise RuntimeError("a CUDA device is required")
         return torch
 
-    def _workspace(self, n, stream):
+    def _workspace(self, n, stream, prec=PBCG_PREC_NONE):
         torch = self._torch()
-        nbytes = pbicgstab_workspace_bytes(n)
+        nbytes = pbicgstab_workspace_bytes_prec(n) if prec == PBCG_PREC_JACOBI else pbicgstab_workspace_bytes(n)
         ws = torch.empty(nbytes // 8 + 64, dtype=torch.float64, device="cuda")
         base = ws.data_ptr()
         aligned = (base + 255) // 256 * 256
@@ -262,21 +338,20 @@ class Solver:
         return aligned, nbytes
 
     @classmethod
-    def from_csr(cls, A, stream=None) -> "Solver":
+    def from_csr(cls, A, stream=None, prec=PBCG_PREC_NONE) -> "Solver":
         self = cls()
         torch = self._torch()
         rowptr = torch.as_tensor(A.rowptr, dtype=torch.int32).cuda()
         col = torch.as_tensor(A.col, dtype=torch.int32).cuda()
         val = torch.as_tensor(A.val, dtype=torch.float64).cuda()
         self._keep += [rowptr, col, val]
-        ws, nb = self._workspace(A.n, stream)
+        ws, nb = self._workspace(A.n, stream, prec)
         self.h = pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), col.data_ptr() if A.nnz else None,
-                                      val.data_ptr() if A.nnz else None, PBCG_PREC_NONE, ws, nb,
-                                      self.stream.cuda_stream)
+                                      val.data_ptr() if A.nnz else None, prec, ws, nb, self.stream.cuda_stream)
         return self
 
     @classmethod
-    def from_stencil(cls, st, stream=None) -> "Solver":
+    def from_stencil(cls, st, stream=None, prec=PBCG_PREC_NONE) -> "Solver":
         self = cls()
         torch = self._torch()
         desc = PbcgStencil()
@@ -296,8 +371,8 @@ class Solver:
                 cd.data2 = t2.data_ptr()
                 cd.len2 = t2.numel()
                 cd.stride2[:] = [int(v) for v in c.stride2]
-        ws, nb = self._workspace(st.n, stream)
-        self.h = pbicgstab_create_stencil(desc, PBCG_PREC_NONE, ws, nb, self.stream.cuda_stream)
+        ws, nb = self._workspace(st.n, stream, prec)
+        self.h = pbicgstab_create_stencil(desc, prec, ws, nb, self.stream.cuda_stream)
         return self
 
     def spmv(self, x):

@@ -283,41 +283,90 @@ def dense_to_csr(a: np.ndarray) -> CSR:
 
 
 def random_sparse(n: int, seed: int, nnz_lo: int = 8, nnz_hi: int = 32, dominance: float = 1.1) -> CSR:
-    """Random unsymmetric sparse matrix: per row k ~ U{nnz_lo..nnz_hi} off-diagonals at
-    distinct uniform random columns (diagonal excluded), values N(0,1) (Box-Muller
-    on SplitMix64 uniforms), diagonal = dominance * row's sum of |off-diagonal|.
+    """Random unsymmetric sparse matrix: row r gets k_r ~ U{nnz_lo..nnz_hi}
+    off-diagonal entries at distinct uniformly random columns (diagonal
+    excluded; duplicates redrawn), values N(0,1) (Box-Muller on SplitMix64
+    uniforms), and diagonal = dominance * the row's sum of |off-diagonal|.
     """
-    rng_u = lambda cnt, start: (splitmix64(seed, cnt, start) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    if n < 2:
+        raise ValueError("n >= 2 required")
     kspan = nnz_hi - nnz_lo + 1
     counts = nnz_lo + (splitmix64(seed ^ 0x5EED, n) % np.uint64(kspan)).astype(np.int64)
     counts = np.minimum(counts, n - 1)
+    total = int(counts.sum())
+    rows = np.repeat(np.arange(n, dtype=np.int64), counts)
+    stream = 0
+
+    def draw(rr, cnt):
+        nonlocal stream
+        d = (splitmix64(seed, cnt, start=stream) % np.uint64(n - 1)).astype(np.int64)
+        stream += cnt
+        return d + (d >= rr)          # skip the diagonal
+
+    cols = draw(rows, total)
+    for _ in range(1000):
+        key = np.sort(rows * n + cols)          # rows sorted, columns sorted within a row
+        rows, cols = key // n, key % n
+        dup = np.zeros(total, dtype=bool)
+        dup[1:] = key[1:] == key[:-1]
+        m = int(dup.sum())
+        if m == 0:
+            break
+        cols[dup] = draw(rows[dup], m)
+    u = (splitmix64(seed ^ 0xA5A5A5A5, 2 * total) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    g = np.sqrt(-2.0 * np.log1p(-u[:total])) * np.cos(2.0 * np.pi * u[total:])
+    diag = dominance * np.bincount(rows, weights=np.abs(g), minlength=n)
+    allr = np.concatenate([rows, np.arange(n, dtype=np.int64)])
+    allc = np.concatenate([cols, np.arange(n, dtype=np.int64)])
+    allv = np.concatenate([g, diag])
+    order = np.argsort(allr * n + allc)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts + 1, out=rowptr[1:])
-    nnz = int(rowptr[-1])
-    col = np.empty(nnz, dtype=np.int32)
-    val = np.empty(nnz, dtype=np.float64)
-    cursor = 0
-    for r in range(n):
-        k = int(counts[r])
-        # distinct columns != r by partial Fisher-Yates over [0, n-1) mapped around r
-        draws = splitmix64(seed + 7919 * (r + 1), k)
-        chosen = {}
-        picks = []
-        for t in range(k):
-            span_t = n - 1 - t
-            jdx = t + int(draws[t] % np.uint64(span_t))
-            a_t, a_j = chosen.get(t, t), chosen.get(jdx, jdx)
-            chosen[t], chosen[jdx] = a_j, a_t
-            picks.append(a_j)
-        cols = np.array([c if c < r else c + 1 for c in picks], dtype=np.int64)
-        u1 = rng_u(k, 2 * cursor + 1)
-        u2 = rng_u(k, 2 * cursor + 1 + k)
-        g = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
-        allc = np.concatenate([cols, [r]])
-        allv = np.concatenate([g, [dominance * np.sum(np.abs(g))]])
-        order = np.argsort(allc)
-        s = int(rowptr[r])
-        col[s:s + k + 1] = allc[order]
-        val[s:s + k + 1] = allv[order]
-        cursor += k + 1
-    return CSR(n=n, rowptr=rowptr.astype(np.int32), col=col, val=val)
+    return CSR(n=n, rowptr=rowptr.astype(np.int32), col=allc[order].astype(np.int32), val=allv[order])
+
+
+@dataclass
+class Batch:
+    """Independent systems concatenated: system s owns rows row_offset[s]..row_offset[s+1]."""
+    sizes: np.ndarray        # int64 [nsys]
+    row_offset: np.ndarray   # int64 [nsys+1]
+    rowptr: np.ndarray       # int32 [total+1], offsets into col/val
+    col: np.ndarray          # int32, local to the system
+    val: np.ndarray          # float64
+    b: np.ndarray            # float64 [total]
+
+    @property
+    def nsys(self) -> int:
+        return int(self.sizes.size)
+
+    @property
+    def total_rows(self) -> int:
+        return int(self.row_offset[-1])
+
+    def system(self, s: int) -> CSR:
+        r0, r1 = int(self.row_offset[s]), int(self.row_offset[s + 1])
+        rp = self.rowptr[r0:r1 + 1].astype(np.int64)
+        e0, e1 = int(rp[0]), int(rp[-1])
+        return CSR(n=r1 - r0, rowptr=(rp - e0).astype(np.int32), col=self.col[e0:e1], val=self.val[e0:e1])
+
+
+def random_batch(nsys: int = 512, seed: int = 0, nmin: int = 1000, nmax: int = 64000,
+                 nnz_lo: int = 8, nnz_hi: int = 32) -> Batch:
+    """nsys random_sparse systems with sizes log-uniform in [nmin, nmax] and
+    b ~ U[-1, 1], ordered largest first (which balances a work queue)."""
+    u = (splitmix64(seed ^ 0xB47C4, nsys) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    sizes = np.rint(np.exp(np.log(nmin) + u * (np.log(nmax) - np.log(nmin)))).astype(np.int64)
+    sizes = np.sort(sizes)[::-1].copy()
+    mats = [random_sparse(int(n), seed * 100003 + 17 * s + 1, nnz_lo, nnz_hi) for s, n in enumerate(sizes)]
+    row_offset = np.zeros(nsys + 1, dtype=np.int64)
+    np.cumsum(sizes, out=row_offset[1:])
+    nnz = np.array([m.nnz for m in mats], dtype=np.int64)
+    nnz_off = np.zeros(nsys + 1, dtype=np.int64)
+    np.cumsum(nnz, out=nnz_off[1:])
+    if nnz_off[-1] >= 2 ** 31:
+        raise ValueError("total nnz does not fit int32")
+    rowptr = np.concatenate([m.rowptr[:-1].astype(np.int64) + nnz_off[s] for s, m in enumerate(mats)] +
+                            [nnz_off[-1:]])
+    b = splitmix64_uniform(seed ^ 0xBBBB, int(row_offset[-1]))
+    return Batch(sizes=sizes, row_offset=row_offset, rowptr=rowptr.astype(np.int32),
+                 col=np.concatenate([m.col for m in mats]), val=np.concatenate([m.val for m in mats]), b=b)

@@ -1,0 +1,97 @@
+"""Batched solves on the GPU: many independent systems in one launch (needs a GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01395_gb300 import native, problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    native.build()
+
+
+def small_batch():
+    return P.random_batch(nsys=24, seed=3, nmin=50, nmax=4000)
+
+
+def test_batched_final_solutions_match_oracle():
+    """Each system solved to rtol 1e-12 (replacement every 20) matches the oracle's
+    solution of that system to 1e-9, and iteration counts agree within 10 %."""
+    import torch
+    B = small_batch()
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    bs.launch(b, x, rtol=1e-12, maxit=3000, replace_period=20)
+    res = bs.fetch_results()
+    xg = x.cpu().numpy()
+    for s in range(B.nsys):
+        A = B.system(s)
+        r0, r1 = B.row_offset[s], B.row_offset[s + 1]
+        ref = oracle.pbicgstab(A, B.b[r0:r1], rtol=1e-12, maxit=3000, replace_period=20)
+        assert res["status"][s] == native.PBCG_OK, s
+        assert abs(res["iters"][s] - ref.iters) <= max(3, 0.1 * ref.iters), s
+        xs = xg[r0:r1]
+        assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-9, s
+        true_rel = np.linalg.norm(B.b[r0:r1] - oracle.spmv(A, xs)) / ref.nr0
+        assert abs(true_rel - res["rel_res_true"][s]) <= 1e-3 * true_rel + 1e-15
+
+
+def test_batched_first_iterations_match_single_system_solver():
+    """A batch of one system takes the same iterations as the single-system
+    oracle, step by step over the first iterations."""
+    import torch
+    B = P.random_batch(nsys=1, seed=9, nmin=3000, nmax=3000)
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    res = bs.fetch_results()
+    ref = oracle.pbicgstab(B.system(0), B.b, rtol=1e-8, maxit=1000)
+    assert res["status"][0] == native.PBCG_OK
+    assert abs(res["iters"][0] - ref.iters) <= 2
+
+
+def test_invalid_system_is_isolated():
+    import torch
+    B = small_batch()
+    col = B.col.copy()
+    e0 = int(B.rowptr[B.row_offset[5]])
+    col[e0] = int(B.sizes[5]) + 7          # out of range for system 5
+    B.col = col
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    res = bs.fetch_results()
+    assert res["status"][5] == native.PBCG_ERR_ARG
+    others = np.delete(res["status"], 5)
+    assert np.all(others == native.PBCG_OK)
+
+
+def test_batched_launch_replays_in_a_cuda_graph():
+    import torch
+    B = small_batch()
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    torch.cuda.synchronize()
+    direct = x.clone()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    x.zero_()
+    with torch.cuda.graph(g, stream=s):
+        x.zero_()
+        bs.launch(b, x, rtol=1e-8, maxit=1000, stream=s)
+    x.fill_(123.0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, direct)
+    assert np.all(bs.fetch_results()["status"] == native.PBCG_OK)

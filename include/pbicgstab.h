@@ -264,6 +264,26 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows,
                                     double rtol, int32_t maxit, int32_t replace_period, void *d_workspace,
                                     size_t ws_bytes, pbcg_batch_result *d_results, void *stream);
 
+/* Adjoint solves (an extension: reverse-mode gradients through a solve; the
+ * paper has no counterpart). For x = A^{-1} b and a loss L(x), lambda solves
+ * A^T lambda = dL/dx; then dL/db = lambda and dL/da_ij = -lambda_i x_j. */
+
+/* Work buffer bytes of pbicgstab_csr_transpose. */
+size_t pbicgstab_transpose_work_bytes(int32_t n);
+
+/* A^T of an n x n CSR matrix into caller-owned arrays d_trowptr[n+1],
+ * d_tcol[nnz], d_tval[nnz]; rows of A^T sorted by column (deterministic).
+ * The input structure is validated on the device (one synchronisation);
+ * invalid input returns PBCG_ERR_ARG. Otherwise asynchronous on `stream`. */
+pbcg_status pbicgstab_csr_transpose(int32_t n, int32_t nnz, const int32_t *d_rowptr, const int32_t *d_col,
+                                    const double *d_val, int32_t *d_trowptr, int32_t *d_tcol, double *d_tval,
+                                    void *d_work, size_t work_bytes, void *stream);
+
+/* d_grad[k] = -d_lambda[i] * d_x[d_col[k]] for every stored entry k of row i
+ * (dL/da_ij). Asynchronous on `stream`. */
+pbcg_status pbicgstab_csr_value_grad(int32_t n, const int32_t *d_rowptr, const int32_t *d_col,
+                                     const double *d_lambda, const double *d_x, double *d_grad, void *stream);
+
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
 #define PBCG_NOALLOC_MAX_N 32768
 

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "pbicgstab.h"
+#include "adjoint.cuh"
 #include "solvers.cuh"
 
 namespace {
@@ -569,6 +570,63 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     if (grid > batch->nsys) grid = batch->nsys;
     PBCG_CUDA(cudaMemsetAsync(B.next, 0, sizeof(unsigned), st));
     pbcg::batched_kernel<<<grid, pbcg::kTPB, 0, st>>>(B);
+    PBCG_CUDA(cudaGetLastError());
+    return PBCG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint building blocks: transpose and value gradient.
+// ---------------------------------------------------------------------------
+extern "C" size_t pbicgstab_transpose_work_bytes(int32_t n) {
+    if (n < 0) return 0;
+    const size_t b = (size_t)(n + 1) * sizeof(int);
+    return b < 256 ? 256 : b;   // also holds the structure-check flag
+}
+
+extern "C" pbcg_status pbicgstab_csr_transpose(int32_t n, int32_t nnz, const int32_t *d_rowptr,
+                                               const int32_t *d_col, const double *d_val, int32_t *d_trowptr,
+                                               int32_t *d_tcol, double *d_tval, void *d_work, size_t work_bytes,
+                                               void *stream) {
+    if (n < 0 || nnz < 0) return fail(PBCG_ERR_ARG, "n and nnz must be >= 0");
+    if (!d_rowptr || !d_trowptr || (nnz > 0 && (!d_col || !d_val || !d_tcol || !d_tval)))
+        return fail(PBCG_ERR_ARG, "CSR array is NULL");
+    if (!d_work || work_bytes < pbicgstab_transpose_work_bytes(n)) return fail(PBCG_ERR_OOM, "work buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    PBCG_CUDA(cudaGetDevice(&dev));
+    PBCG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // validate the input structure first (columns index rows of A^T)
+    pbicgstab_s h{};
+    h.num_sms = sms;
+    h.stream = st;
+    h.ctl = (pbcg::Control *)d_work;   // the check flag lives in the work buffer's first word
+    pbcg_status s0 = check_csr(&h, n, nnz, d_rowptr, d_col);
+    if (s0 != PBCG_OK) return s0;
+    int *cursor = (int *)d_work;
+    const int blocks = 4 * sms;
+    PBCG_CUDA(cudaMemsetAsync(d_trowptr, 0, (size_t)(n + 1) * sizeof(int), st));
+    if (nnz > 0) pbcg::transpose_count_kernel<<<blocks, 256, 0, st>>>(nnz, d_col, d_trowptr);
+    pbcg::scan_kernel<<<1, 1024, 0, st>>>(n + 1, d_trowptr);
+    PBCG_CUDA(cudaMemsetAsync(cursor, 0, (size_t)(n + 1) * sizeof(int), st));
+    if (n > 0) {
+        pbcg::transpose_scatter_kernel<<<blocks, 256, 0, st>>>(n, d_rowptr, d_col, d_val, d_trowptr, cursor, d_tcol,
+                                                               d_tval);
+        pbcg::sort_rows_kernel<<<blocks, 256, 0, st>>>(n, d_trowptr, d_tcol, d_tval);
+    }
+    PBCG_CUDA(cudaGetLastError());
+    return PBCG_OK;
+}
+
+extern "C" pbcg_status pbicgstab_csr_value_grad(int32_t n, const int32_t *d_rowptr, const int32_t *d_col,
+                                                const double *d_lambda, const double *d_x, double *d_grad,
+                                                void *stream) {
+    if (n < 0) return fail(PBCG_ERR_ARG, "n must be >= 0");
+    if (n == 0) return PBCG_OK;
+    if (!d_rowptr || !d_col || !d_lambda || !d_x || !d_grad) return fail(PBCG_ERR_ARG, "array is NULL");
+    int dev = 0, sms = 0;
+    PBCG_CUDA(cudaGetDevice(&dev));
+    PBCG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    pbcg::value_grad_kernel<<<4 * sms, 256, 0, (cudaStream_t)stream>>>(n, d_rowptr, d_col, d_lambda, d_x, d_grad);
     PBCG_CUDA(cudaGetLastError());
     return PBCG_OK;
 }

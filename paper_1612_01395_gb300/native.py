@@ -31,7 +31,8 @@ PBCG_PREC_NONE, PBCG_PREC_JACOBI = 0, 1
 EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_workspace_bytes_prec", "pbicgstab_create_csr", "pbicgstab_create_stencil",
            "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
            "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
-           "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched"]
+           "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched",
+           "pbicgstab_transpose_work_bytes", "pbicgstab_csr_transpose", "pbicgstab_csr_value_grad"]
 PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
@@ -137,6 +138,12 @@ def lib():
         L.pbicgstab_solve_batched.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32, vp,
                                               sz, vp, vp]
         L.pbicgstab_solve_batched.restype = ctypes.c_int
+        L.pbicgstab_transpose_work_bytes.argtypes = [i32]
+        L.pbicgstab_transpose_work_bytes.restype = sz
+        L.pbicgstab_csr_transpose.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        L.pbicgstab_csr_transpose.restype = ctypes.c_int
+        L.pbicgstab_csr_value_grad.argtypes = [i32, vp, vp, vp, vp, vp, vp]
+        L.pbicgstab_csr_value_grad.restype = ctypes.c_int
         L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
                                                   ctypes.POINTER(PbcgOpts), vp, ctypes.POINTER(PbcgInfo)]
         L.pbicgstab_size.argtypes = [vp]
@@ -291,6 +298,20 @@ class BatchSolver:
                        ("n_replacements", np.int32), ("rel_res_recursive", np.float64),
                        ("rel_res_true", np.float64)])
         return np.frombuffer(raw, dtype=dt, count=self.nsys)
+
+
+def pbicgstab_transpose_work_bytes(n: int) -> int:
+    return int(lib().pbicgstab_transpose_work_bytes(int(n)))
+
+
+def pbicgstab_csr_transpose(n, nnz, d_rowptr, d_col, d_val, d_trowptr, d_tcol, d_tval, d_work, work_bytes,
+                            stream) -> int:
+    return lib().pbicgstab_csr_transpose(int(n), int(nnz), d_rowptr, d_col, d_val, d_trowptr, d_tcol, d_tval,
+                                         d_work, int(work_bytes), stream)
+
+
+def pbicgstab_csr_value_grad(n, d_rowptr, d_col, d_lambda, d_x, d_grad, stream) -> int:
+    return lib().pbicgstab_csr_value_grad(int(n), d_rowptr, d_col, d_lambda, d_x, d_grad, stream)
 
 
 def pbicgstab_spmv(h, d_x, d_y) -> int:

@@ -227,6 +227,24 @@ def cd2d_constant(n: int = 64, c: Sequence[float] = (10.0, 10.0)) -> Stencil:
     return convection_diffusion((n, n), (np.full(n, c[0]), np.full(n, c[1])))
 
 
+def cd2d_field(n: int = 1024, cmax: float = 50.0, seed: int = 0) -> Stencil:
+    """2-D convection-diffusion with a per-cell velocity (c, c), c ~ U[0, cmax]
+    from SplitMix64 (one value per node, lexicographic order): minus-side
+    neighbours -1 - h c, plus-side -1, diagonal 4 + 2 h c (c >= 0, upwind)."""
+    h = 1.0 / (n + 1)
+    c = 0.5 * cmax * (splitmix64_uniform(seed ^ 0xC0FFEE, n * n) + 1.0)
+    minus = -1.0 - h * c
+    coefs = [None] * 7
+    coefs[C] = Coef(table=(2.0 + h * c) + (2.0 + h * c), stride=(1, n, 0))
+    coefs[W] = Coef(table=minus, stride=(1, n, 0))
+    coefs[E] = Coef(value=-1.0)
+    coefs[S] = Coef(table=minus, stride=(1, n, 0))
+    coefs[N] = Coef(value=-1.0)
+    coefs[B] = Coef(value=0.0)
+    coefs[T] = Coef(value=0.0)
+    return Stencil(nx=n, ny=n, nz=1, coefs=coefs)
+
+
 def cd3d_trig(n: int = 256, amp: float = 20.0) -> Stencil:
     """3-D convection-diffusion, velocity (amp sin y, amp cos z, amp sin x), n^3 grid."""
     h = 1.0 / (n + 1)

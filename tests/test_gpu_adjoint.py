@@ -1,0 +1,92 @@
+"""Adjoint (reverse-mode) solves on the GPU, checked against the oracle's adjoint
+and central finite differences (needs a GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1612_01395_gb300 import native, problems as P
+from test_oracle_adjoint import oracle_gradients, transpose
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    native.build()
+
+
+def test_transpose_matches_scipy_bitwise():
+    import torch
+    from paper_1612_01395_gb300.adjoint import CSRStructure
+    A = P.random_sparse(2000, seed=4)
+    st = CSRStructure(A.rowptr, A.col)
+    val = torch.from_numpy(A.val).cuda()
+    rc = native.pbicgstab_csr_transpose(st.n, st.nnz, st.rowptr.data_ptr(), st.col.data_ptr(), val.data_ptr(),
+                                        st.trowptr.data_ptr(), st.tcol.data_ptr(), st.tval.data_ptr(),
+                                        st.work.data_ptr(), st.work_bytes, torch.cuda.current_stream().cuda_stream)
+    assert rc == native.PBCG_OK
+    T = transpose(A)
+    np.testing.assert_array_equal(st.trowptr.cpu().numpy(), T.rowptr)
+    np.testing.assert_array_equal(st.tcol.cpu().numpy(), T.col)
+    np.testing.assert_array_equal(st.tval.cpu().numpy(), T.val)
+
+
+def setup(n=48, seed=1):
+    import torch
+    from paper_1612_01395_gb300.adjoint import CSRStructure
+    A = P.stencil_to_csr(P.cd2d_field(n, seed=seed))
+    b = P.splitmix64_uniform(2, A.n)
+    xt = P.splitmix64_uniform(3, A.n)
+    return A, b, xt, CSRStructure(A.rowptr, A.col)
+
+
+def gpu_loss_and_grads(A, b, xt, st):
+    import torch
+    from paper_1612_01395_gb300.adjoint import sparse_solve
+    vals = torch.from_numpy(A.val).cuda().requires_grad_(True)
+    bt = torch.from_numpy(b).cuda().requires_grad_(True)
+    x = sparse_solve(vals, bt, st, rtol=1e-13)
+    L = 0.5 * ((x - torch.from_numpy(xt).cuda()) ** 2).sum()
+    L.backward()
+    return float(L), x.detach().cpu().numpy(), bt.grad.cpu().numpy(), vals.grad.cpu().numpy()
+
+
+def test_adjoint_gradients_match_oracle_adjoint():
+    A, b, xt, st = setup()
+    L, x, gb, gv = gpu_loss_and_grads(A, b, xt, st)
+    xo, gbo, gvo = oracle_gradients(A, b, xt)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-9
+    assert np.linalg.norm(gb - gbo) / np.linalg.norm(gbo) <= 1e-8
+    assert np.linalg.norm(gv - gvo) / np.linalg.norm(gvo) <= 1e-8
+
+
+def test_adjoint_gradients_match_central_differences():
+    """32 random coordinates of dL/db and dL/dvalues, central differences h = 1e-6."""
+    import torch
+    from paper_1612_01395_gb300.adjoint import sparse_solve
+    A, b, xt, st = setup()
+    L, x, gb, gv = gpu_loss_and_grads(A, b, xt, st)
+    xt_d = torch.from_numpy(xt).cuda()
+    vals0 = torch.from_numpy(A.val).cuda()
+    b0 = torch.from_numpy(b).cuda()
+
+    def f(vals, bb):
+        xx = sparse_solve(vals, bb, st, rtol=1e-13)
+        return float(0.5 * ((xx - xt_d) ** 2).sum())
+
+    h = 1e-6
+    rng_b = (P.splitmix64(11, 16) % np.uint64(A.n)).astype(int)
+    rng_v = (P.splitmix64(12, 16) % np.uint64(A.nnz)).astype(int)
+    for i in rng_b:
+        e = torch.zeros_like(b0)
+        e[i] = h
+        fd = (f(vals0, b0 + e) - f(vals0, b0 - e)) / (2 * h)
+        assert abs(fd - gb[i]) <= 1e-5 * abs(gb[i]) + 1e-8, i
+    for k in rng_v:
+        e = torch.zeros_like(vals0)
+        e[k] = h
+        fd = (f(vals0 + e, b0) - f(vals0 - e, b0)) / (2 * h)
+        assert abs(fd - gv[k]) <= 1e-5 * abs(gv[k]) + 1e-8, k

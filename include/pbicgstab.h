@@ -244,6 +244,16 @@ typedef struct {
     double rel_res_true;
 } pbcg_batch_result;
 
+/* Launch shape of a batched solve. A large system is solved by all CTAs of a
+ * thread-block cluster (rows split between them, reductions through the
+ * cluster's distributed shared memory); a small one by a single CTA.
+ * Zero fields take the defaults. */
+typedef struct {
+    int32_t cluster_size;       /* CTAs per cluster: 1 (no clusters), 2, 4, 8 or 16; 0 = 8 */
+    int32_t pad;
+    int64_t cluster_min_rows;   /* systems with at least this many rows use a whole cluster; 0 = 8192 */
+} pbcg_batch_opts;
+
 /* Workspace of a batched solve: 10 FP64 vectors over all rows + a counter. */
 size_t pbicgstab_batched_workspace_bytes(int64_t total_rows);
 
@@ -251,9 +261,13 @@ size_t pbicgstab_batched_workspace_bytes(int64_t total_rows);
  * residual replacement every replace_period iterations, 0 = off), each to
  * ||r|| <= rtol ||r_0|| of its own, in one launch (an extension of the
  * paper's method to many small systems; no counterpart in the paper).
- * Each system is solved by one thread block with block-level reductions, so
- * systems converge independently; blocks take systems in index order from a
- * counter (order them largest first). Fully asynchronous on `stream`: no host
+ * Systems converge independently: a system with at least
+ * opts->cluster_min_rows rows is solved by the CTAs of one thread-block
+ * cluster together, a smaller one by one CTA with block-level reductions;
+ * clusters take systems in index order from a counter (order them largest
+ * first). opts may be NULL (defaults); an unsupported cluster size returns
+ * PBCG_ERR_ARG, and a cluster shape the GPU cannot make resident returns
+ * PBCG_ERR_CUDA. Fully asynchronous on `stream`: no host
  * synchronisation and no allocation, so a call can be captured into a CUDA
  * graph and replayed. d_b, d_x (in: x0, out: x) span all rows; d_results
  * receives nsys pbcg_batch_result in device memory; the workspace must stay
@@ -261,8 +275,8 @@ size_t pbicgstab_batched_workspace_bytes(int64_t total_rows);
  * device per system (an invalid system gets PBCG_ERR_ARG and is skipped).
  * Host-side argument errors return PBCG_ERR_ARG immediately. */
 pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows, const double *d_b, double *d_x,
-                                    double rtol, int32_t maxit, int32_t replace_period, void *d_workspace,
-                                    size_t ws_bytes, pbcg_batch_result *d_results, void *stream);
+                                    double rtol, int32_t maxit, int32_t replace_period, const pbcg_batch_opts *opts,
+                                    void *d_workspace, size_t ws_bytes, pbcg_batch_result *d_results, void *stream);
 
 /* Adjoint solves (an extension: reverse-mode gradients through a solve; the
  * paper has no counterpart). For x = A^{-1} b and a loss L(x), lambda solves

@@ -5,7 +5,7 @@
  * the parallel solution of large unsymmetric linear systems" (arXiv:1612.01395).
  *
  * This file is the plain, slow, single-threaded reference that the CUDA path
- * is judged against. Only the test suite, the smoke check and the benchmark's
+ * is checked against. Only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg may load it. It shares no code with the CUDA library.
  *
  * Every routine follows the paper's algorithm step by step, in the paper's

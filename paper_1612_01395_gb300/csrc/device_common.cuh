@@ -234,4 +234,94 @@ __device__ __forceinline__ bool grid_sum(BlockSync &g, double (&v)[K], double (*
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Thread-block clusters (batched solves of large systems). The CTAs of a
+// cluster are co-scheduled by the hardware, so a wait on the hardware cluster
+// barrier always completes once every CTA reaches it; each CTA can address
+// the shared memory of the others (distributed shared memory).
+// ---------------------------------------------------------------------------
+constexpr int kMaxCluster = 16;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_ctas() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives and waits. Release on
+// arrival and acquire on the wait (cluster scope) order each CTA's earlier
+// stores -- global and shared -- before the other CTAs' later loads.
+// (The non-.aligned forms: no requirement that a warp arrives converged.)
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// Address of *p (a __shared__ object of this CTA) in the shared memory of CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_map(const void *p, unsigned rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ void st_cluster_f64(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t addr) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Synchronisation policy of a solve shared by the `size` CTAs of a cluster:
+// a barrier is the cluster barrier; a reduction publishes each CTA's block
+// sums into its slot in the shared memory of CTA 0 (two alternating buffers),
+// crosses the barrier, and every CTA adds the slots in rank order -- the same
+// additions in the same order everywhere, so all CTAs hold identical scalars.
+// A slot buffer is rewritten two reductions later, after the barrier of the
+// reduction in between, which every CTA reaches only when it has finished
+// reading. Same interface as GridSync and BlockSync.
+struct ClusterSync {
+    uint32_t slots0;    // cluster address of CTA 0's slot array [2][kMaxCluster][kSlotDoubles]
+    double *bcast;      // this CTA's shared [kMaxDots]: the cluster sums, for every thread
+    unsigned rank, size;
+    unsigned epoch;     // reductions done
+    int count;
+};
+
+__device__ __forceinline__ bool grid_sync(ClusterSync &g, double (*)[32], int *) {
+    cluster_barrier();
+    g.count++;
+    return true;
+}
+
+template <int K>
+__device__ __forceinline__ bool grid_sum(ClusterSync &g, double (&v)[K], double (*sm)[32], int *) {
+    block_sum<K>(v, sm);   // ends with __syncthreads; every thread holds the block sums
+    const uint32_t buf = g.slots0 + (g.epoch & 1u) * (uint32_t)(kMaxCluster * kSlotDoubles * sizeof(double));
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) st_cluster_f64(buf + (g.rank * kSlotDoubles + k) * sizeof(double), v[k]);
+    }
+    cluster_barrier();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (unsigned r = 0; r < g.size; ++r)
+            t += ld_cluster_f64(buf + (r * kSlotDoubles + threadIdx.x) * sizeof(double));
+        g.bcast[threadIdx.x] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = g.bcast[k];
+    __syncthreads();
+    g.epoch++;
+    g.count++;
+    return true;
+}
+
 }  // namespace pbcg

@@ -528,8 +528,8 @@ extern "C" size_t pbicgstab_batched_workspace_bytes(int64_t total_rows) {
 
 extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows, const double *d_b,
                                                double *d_x, double rtol, int32_t maxit, int32_t replace_period,
-                                               void *d_workspace, size_t ws_bytes, pbcg_batch_result *d_results,
-                                               void *stream) {
+                                               const pbcg_batch_opts *opts, void *d_workspace, size_t ws_bytes,
+                                               pbcg_batch_result *d_results, void *stream) {
     if (!batch) return fail(PBCG_ERR_ARG, "batch is NULL");
     if (batch->nsys < 0 || batch->nnz < 0 || total_rows < 0) return fail(PBCG_ERR_ARG, "negative size");
     if (batch->nsys == 0) return PBCG_OK;
@@ -541,12 +541,15 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     if (ws_bytes < pbicgstab_batched_workspace_bytes(total_rows))
         return fail(PBCG_ERR_OOM, "workspace has %zu bytes, needs %zu", ws_bytes,
                     pbicgstab_batched_workspace_bytes(total_rows));
+    int csize = opts && opts->cluster_size ? opts->cluster_size : 8;
+    const long long cmin = opts && opts->cluster_min_rows ? opts->cluster_min_rows : 8192;
+    if (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)
+        return fail(PBCG_ERR_ARG, "cluster_size must be 1, 2, 4, 8 or 16 (got %d)", csize);
+    if (cmin < 0) return fail(PBCG_ERR_ARG, "cluster_min_rows must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     PBCG_CUDA(cudaGetDevice(&dev));
     PBCG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::batched_kernel, pbcg::kTPB, 0));
-    if (occ < 1) return fail(PBCG_ERR_CUDA, "batched kernel cannot be resident on an SM");
     pbcg::BatchArgs B;
     B.nsys = batch->nsys;
     B.nnz = batch->nnz;
@@ -566,11 +569,41 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     B.rtol = rtol;
     B.maxit = maxit;
     B.replace_period = replace_period;
-    int grid = occ * sms;
-    if (grid > batch->nsys) grid = batch->nsys;
+    B.cluster_min_rows = cmin;
+
+    // One resident wave of clusters; clusters take systems until none is left.
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(pbcg::kTPB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    int grid = 0;
+    if (csize > 1) {
+        if (csize > 8)
+            PBCG_CUDA(cudaFuncSetAttribute(pbcg::batched_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3((unsigned)(csize * sms));
+        int clusters = 0;
+        PBCG_CUDA(cudaOccupancyMaxActiveClusters(&clusters, pbcg::batched_kernel, &cfg));
+        if (clusters < 1) return fail(PBCG_ERR_CUDA, "clusters of %d CTAs cannot be resident", csize);
+        grid = clusters * csize;
+    } else {
+        int occ = 0;
+        PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::batched_kernel, pbcg::kTPB, 0));
+        if (occ < 1) return fail(PBCG_ERR_CUDA, "batched kernel cannot be resident on an SM");
+        grid = occ * sms;
+        if (grid > batch->nsys) grid = batch->nsys;
+        cfg.attrs = nullptr;
+        cfg.numAttrs = 0;
+    }
+    cfg.gridDim = dim3((unsigned)grid);
     PBCG_CUDA(cudaMemsetAsync(B.next, 0, sizeof(unsigned), st));
-    pbcg::batched_kernel<<<grid, pbcg::kTPB, 0, st>>>(B);
-    PBCG_CUDA(cudaGetLastError());
+    PBCG_CUDA(cudaLaunchKernelEx(&cfg, pbcg::batched_kernel, B));
     return PBCG_OK;
 }
 

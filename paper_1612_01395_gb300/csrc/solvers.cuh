@@ -129,6 +129,46 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
     }
 }
 
+// Per-thread accumulation of a dot product over the rows of a sweep. FP64
+// vectors: an FMA into a double. FP32 vectors (the inner solves of the
+// mixed-precision refinement): compensated FP32 accumulation, algorithm Dot2
+// of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26, 2005): each product is split exactly into its rounded value and
+// rounding error (TwoProduct by FMA), the running sum is updated by the
+// error-free TwoSum and all errors are summed apart; the result is as accurate
+// as if accumulated in twice the working precision and is converted to double
+// once per thread and sweep. On this GPU an FP32 operation costs 1/64 of an
+// FP64 one, so the inner solves keep FP64-grade dot products without any FP64
+// instruction per row. Explicit _rn intrinsics keep the compiler from fusing
+// the steps of the error-free transformations.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = __fmaf_rn(a, b, -p);   // a b - p, exactly
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p - t, exactly
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(e, pe));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <typename T, int K>
+__device__ __forceinline__ void dot_values(const DotAcc<T> (&acc)[K], double (&d)[K]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) d[k] = acc[k].value();
+}
+
 // ===========================================================================
 // Algorithm 9 (pipelined BiCGStab) with the residual replacement of
 // Section 4.2 (r := b - A x, w := A r before the second reduction of iteration
@@ -146,16 +186,20 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     const bool fixed = a.fixed != 0;
 
     // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
-    double d0[1] = {0.0};
-    PBCG_ROWS(i) {
-        const T ri = a.b[i] - A.row(i, VecLoadT<T>{x});
-        V.r[i] = ri;
-        V.r0[i] = ri;
-        V.p[i] = T(0);
-        V.s[i] = T(0);
-        V.z[i] = T(0);
-        V.v[i] = T(0);
-        d0[0] = fma((double)ri, (double)ri, d0[0]);
+    double d0[1];
+    {
+        DotAcc<T> acc[1];
+        PBCG_ROWS(i) {
+            const T ri = a.b[i] - A.row(i, VecLoadT<T>{x});
+            V.r[i] = ri;
+            V.r0[i] = ri;
+            V.p[i] = T(0);
+            V.s[i] = T(0);
+            V.z[i] = T(0);
+            V.v[i] = T(0);
+            acc[0].add(ri, ri);
+        }
+        dot_values(acc, d0);
     }
     ++spmvs;
     if (!grid_sum<1>(g, d0, sm, sflag)) return false;
@@ -167,11 +211,14 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
 
     // w_0 := A r_0; alpha_0 := (r0, r0) / (r0, w0)
-    d0[0] = 0.0;
-    PBCG_ROWS(i) {
-        const T wi = A.row(i, VecLoadT<T>{V.r});
-        V.w[i] = wi;
-        d0[0] = fma((double)V.r0[i], (double)wi, d0[0]);
+    {
+        DotAcc<T> acc[1];
+        PBCG_ROWS(i) {
+            const T wi = A.row(i, VecLoadT<T>{V.r});
+            V.w[i] = wi;
+            acc[0].add(V.r0[i], wi);
+        }
+        dot_values(acc, d0);
     }
     ++spmvs;
     if (!grid_sum<1>(g, d0, sm, sflag)) return false;
@@ -183,7 +230,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     int it = 0;
     while (it < a.limit) {
         // ---- phase A: t_i = A w_i; p_i, s_i, z_i, q_i, y_i; first reduction
-        double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
+        DotAcc<T> a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         const T al = (T)alpha, be = (T)beta, om = (T)omega;
         if (!replaced_rw) {
             PBCG_ROWS(i) {
@@ -200,12 +247,12 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                 V.z[i] = zn;
                 V.q[i] = qi;
                 V.y[i] = yi;
-                const double r0d = V.r0[i], qd = qi, yd = yi;
-                d1[0] = fma(qd, yd, d1[0]);
-                d1[1] = fma(yd, yd, d1[1]);
-                d1[2] = fma(qd, qd, d1[2]);
-                d1[3] = fma(r0d, (double)sn, d1[3]);
-                d1[4] = fma(r0d, (double)zn, d1[4]);
+                const T r0i = V.r0[i];
+                a1[0].add(qi, yi);
+                a1[1].add(yi, yi);
+                a1[2].add(qi, qi);
+                a1[3].add(r0i, sn);
+                a1[4].add(r0i, zn);
             }
             ++spmvs;
         } else {
@@ -225,15 +272,17 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                 V.z[i] = zn;
                 V.q[i] = qi;
                 V.y[i] = yi;
-                const double r0d = V.r0[i], qd = qi, yd = yi;
-                d1[0] = fma(qd, yd, d1[0]);
-                d1[1] = fma(yd, yd, d1[1]);
-                d1[2] = fma(qd, qd, d1[2]);
-                d1[3] = fma(r0d, (double)sn, d1[3]);
-                d1[4] = fma(r0d, (double)zn, d1[4]);
+                const T r0i = V.r0[i];
+                a1[0].add(qi, yi);
+                a1[1].add(yi, yi);
+                a1[2].add(qi, qi);
+                a1[3].add(r0i, sn);
+                a1[4].add(r0i, zn);
             }
             spmvs += 3;
         }
+        double d1[5];
+        dot_values(a1, d1);
         if (!grid_sum<5>(g, d1, sm, sflag)) return false;
         const double qy = d1[0], yy = d1[1], qq = d1[2], r0s = d1[3], r0z = d1[4];
         if (!all_finite(d1)) { o.status = PBCG_NONFINITE; break; }
@@ -255,7 +304,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         // ---- phase B: v_i = A z_i; x_{i+1}, r_{i+1}, w_{i+1}; second reduction
         const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
                                  (a.max_repl < 0 || o.nrr < a.max_repl);
-        double d2[3] = {0.0, 0.0, 0.0};   // (r0,r) (r0,w) (r,r)
+        DotAcc<T> a2[3];   // (r0,r) (r0,w) (r,r)
         const T om2 = (T)omega;
         if (!replace_now) {
             PBCG_ROWS(i) {
@@ -267,10 +316,10 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                 V.v[i] = vi;
                 V.r[i] = rn;
                 V.w[i] = wn;
-                const double r0d = V.r0[i], rd = rn;
-                d2[0] = fma(r0d, rd, d2[0]);
-                d2[1] = fma(r0d, (double)wn, d2[1]);
-                d2[2] = fma(rd, rd, d2[2]);
+                const T r0i = V.r0[i];
+                a2[0].add(r0i, rn);
+                a2[1].add(r0i, wn);
+                a2[2].add(rn, rn);
             }
             ++spmvs;
         } else {
@@ -281,15 +330,17 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const T wn = A.row(i, VecLoadT<T>{V.r});
-                const double rd = V.r[i], r0d = V.r0[i];
+                const T ri = V.r[i], r0i = V.r0[i];
                 V.w[i] = wn;
-                d2[0] = fma(r0d, rd, d2[0]);
-                d2[1] = fma(r0d, (double)wn, d2[1]);
-                d2[2] = fma(rd, rd, d2[2]);
+                a2[0].add(r0i, ri);
+                a2[1].add(r0i, wn);
+                a2[2].add(ri, ri);
             }
             spmvs += 2;
             o.nrr++;
         }
+        double d2[3];
+        dot_values(a2, d2);
         replaced_rw = replace_now;
         if (!grid_sum<3>(g, d2, sm, sflag)) return false;
         ++it;
@@ -920,15 +971,20 @@ __global__ void jacobi_stencil_kernel(const StencilOp A, double *minv, int *bad)
 }
 
 // ===========================================================================
-// Batched solves: many independent systems in one launch. Each block takes the
-// next system from an atomic counter and solves it alone with Algorithm 9
-// (block-level reductions and barriers, BlockSync), so systems converge
-// independently and blocks never wait on each other -- no co-residency is
-// needed and the launch can be captured in a CUDA graph. System s owns the
-// global rows [row_offset[s], row_offset[s+1]) of the concatenated CSR arrays
-// (row pointers index the shared col/val arrays; column indices are local to
-// the system) and of b, x and the work vectors. Systems are taken in index
-// order; ordering them largest first balances the load.
+// Batched solves: many independent systems in one launch. The launch is made
+// of thread-block clusters of `size` CTAs (size 1: plain blocks). The first
+// CTA of a cluster takes the next system from an atomic counter; a system with
+// at least `cluster_min_rows` rows is solved by the whole cluster (rows split
+// into `size` contiguous ranges, reductions through distributed shared memory
+// and the hardware cluster barrier, ClusterSync); otherwise the first CTA
+// takes `size` - 1 further systems and every CTA solves one alone (block-level
+// reductions and barriers, BlockSync). Clusters never wait on each other, so
+// no co-residency beyond the cluster is needed and the launch can be captured
+// in a CUDA graph. System s owns the global rows [row_offset[s],
+// row_offset[s+1]) of the concatenated CSR arrays (row pointers index the
+// shared col/val arrays; column indices are local to the system) and of b, x
+// and the work vectors. Systems are taken in index order; ordering them
+// largest first balances the load.
 // ===========================================================================
 struct BatchArgs {
     int nsys;
@@ -946,71 +1002,116 @@ struct BatchArgs {
     double rtol;
     int maxit;
     int replace_period;
+    long long cluster_min_rows;    // systems this large are solved by a whole cluster
 };
+
+// Solve system `sys` on rows [lo, hi) of it (the whole system for BlockSync,
+// this CTA's share for ClusterSync); the first CTA writes the result.
+template <class Sync>
+__device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync &g, unsigned part, unsigned parts,
+                                               double (*sm)[32], int *sflag) {
+    const long long r0 = B.row_offset[sys], r1 = B.row_offset[sys + 1];
+    // structure check of this system: its rows inside the batch, entries inside
+    // the shared arrays, columns local to the system (each CTA checks its rows)
+    int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
+    const int n = bad ? 0 : (int)(r1 - r0);
+    const int lo = (int)((long long)part * n / parts), hi = (int)((long long)(part + 1) * n / parts);
+    const CsrOp A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
+    PBCG_ROWS(i) {
+        const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
+        if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
+        for (int k = e0; k < e1 && !bad; ++k)
+            if (B.col[k] < 0 || B.col[k] >= n) bad = 1;
+    }
+    double fb[1] = {(double)bad};
+    grid_sum<1>(g, fb, sm, sflag);
+    pbcg_batch_result res{0, PBCG_ERR_ARG, 0, 0, 0.0, 0.0};
+    if (fb[0] == 0.0) {
+        SolveArgs a;
+        a.n = n;
+        a.b = B.b + r0;
+        a.x = B.x + r0;
+        a.V = Vectors{B.V.r + r0, B.V.r0 + r0, B.V.p + r0, B.V.s + r0, B.V.z + r0,
+                      B.V.q + r0, B.V.y + r0, B.V.w + r0, B.V.t + r0, B.V.v + r0};
+        a.ctl = nullptr;
+        a.partials = nullptr;
+        a.hist = nullptr;
+        a.rtol = B.rtol;
+        a.limit = B.maxit;
+        a.fixed = 0;
+        a.replace_period = B.replace_period;
+        a.max_repl = -1;
+        a.variant = 0;
+        a.minv = nullptr;
+        a.rh = a.sh = a.zh = a.qh = a.wh = nullptr;
+        Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+        int spmvs = 0;
+        pipelined_loop<CsrOp, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
+        // true residual of the returned x
+        double d[1] = {0.0};
+        PBCG_ROWS(i) {
+            const double rr = a.b[i] - A.row(i, VecLoad{a.x});
+            d[0] = fma(rr, rr, d[0]);
+        }
+        grid_sum<1>(g, d, sm, sflag);
+        res.iters = o.iters;
+        res.status = o.status;
+        res.half_step = o.half;
+        res.n_replacements = o.nrr;
+        const double nr = o.iters > 0 ? sqrt(o.nr) : o.nr0;
+        res.rel_res_recursive = o.nr0 > 0.0 ? nr / o.nr0 : 0.0;
+        res.rel_res_true = o.nr0 > 0.0 ? sqrt(d[0]) / o.nr0 : sqrt(d[0]);
+    }
+    if (part == 0 && threadIdx.x == 0) B.out[sys] = res;
+}
 
 __global__ void __launch_bounds__(kTPB) batched_kernel(const BatchArgs B) {
     __shared__ double sm[kMaxDots][32];
+    __shared__ double slots[2][kMaxCluster][kSlotDoubles];   // used in CTA 0 of a cluster
+    __shared__ double bcast[kMaxDots];
+    __shared__ int item[2];   // system of this CTA (-1: none), whole-cluster flag (-1: no work left)
     __shared__ int sflag;
-    __shared__ int s_sys;
+    const unsigned size = cluster_ctas(), rank = cluster_rank();
+    if (size > 1) cluster_barrier();   // every CTA started before its shared memory is addressed
     for (;;) {
-        if (threadIdx.x == 0) s_sys = (int)atomicAdd(B.next, 1u);
-        __syncthreads();
-        const int sys = s_sys;
-        __syncthreads();
-        if (sys >= B.nsys) return;
-        const long long r0 = B.row_offset[sys], r1 = B.row_offset[sys + 1];
-        // structure check of this system: its rows inside the batch, entries inside
-        // the shared arrays, columns local to the system
-        int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
-        const int n = bad ? 0 : (int)(r1 - r0);
-        const CsrOp A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
-        for (int i = threadIdx.x; i < n; i += kTPB) {
-            const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
-            if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
-            for (int k = e0; k < e1 && !bad; ++k)
-                if (B.col[k] < 0 || B.col[k] >= n) bad = 1;
-        }
-        bad = __syncthreads_or(bad);
-        pbcg_batch_result res{0, PBCG_ERR_ARG, 0, 0, 0.0, 0.0};
-        if (!bad) {
-            SolveArgs a;
-            a.n = n;
-            a.b = B.b + r0;
-            a.x = B.x + r0;
-            a.V = Vectors{B.V.r + r0, B.V.r0 + r0, B.V.p + r0, B.V.s + r0, B.V.z + r0,
-                          B.V.q + r0, B.V.y + r0, B.V.w + r0, B.V.t + r0, B.V.v + r0};
-            a.ctl = nullptr;
-            a.partials = nullptr;
-            a.hist = nullptr;
-            a.rtol = B.rtol;
-            a.limit = B.maxit;
-            a.fixed = 0;
-            a.replace_period = B.replace_period;
-            a.max_repl = -1;
-            a.variant = 0;
-            a.minv = nullptr;
-            a.rh = a.sh = a.zh = a.qh = a.wh = nullptr;
-            BlockSync bs{0};
-            Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
-            int spmvs = 0;
-            pipelined_loop<CsrOp, double, BlockSync>(A, a, bs, sm, &sflag, 0, n, o, spmvs);
-            // true residual of the returned x
-            double d[1] = {0.0};
-            for (int i = threadIdx.x; i < n; i += kTPB) {
-                const double rr = a.b[i] - A.row(i, VecLoad{a.x});
-                d[0] = fma(rr, rr, d[0]);
+        if (rank == 0 && threadIdx.x == 0) {
+            const int s = (int)atomicAdd(B.next, 1u);
+            int whole = 0;
+            if (s >= B.nsys) {
+                whole = -1;
+            } else if (size > 1) {
+                const long long rows = B.row_offset[s + 1] - B.row_offset[s];
+                whole = rows >= B.cluster_min_rows ? 1 : 0;
             }
-            block_sum<1>(d, sm);
-            res.iters = o.iters;
-            res.status = o.status;
-            res.half_step = o.half;
-            res.n_replacements = o.nrr;
-            const double nr = o.iters > 0 ? sqrt(o.nr) : o.nr0;
-            res.rel_res_recursive = o.nr0 > 0.0 ? nr / o.nr0 : 0.0;
-            res.rel_res_true = o.nr0 > 0.0 ? sqrt(d[0]) / o.nr0 : sqrt(d[0]);
+            int extra = 0;
+            if (whole == 0 && size > 1) extra = (int)atomicAdd(B.next, size - 1);
+            for (unsigned r = 0; r < size; ++r) {
+                int mine = s;
+                if (whole == -1) mine = -1;
+                else if (whole == 0 && r > 0) mine = extra + (int)r - 1 < B.nsys ? extra + (int)r - 1 : -1;
+                if (size > 1) {
+                    st_cluster_s32(cluster_map(&item[0], r), mine);
+                    st_cluster_s32(cluster_map(&item[1], r), whole);
+                } else {
+                    item[0] = mine;
+                    item[1] = whole;
+                }
+            }
         }
-        if (threadIdx.x == 0) B.out[sys] = res;
-        __syncthreads();
+        if (size > 1) cluster_barrier();
+        else __syncthreads();
+        const int sys = item[0], whole = item[1];
+        if (whole < 0) return;   // the same for every CTA of the cluster
+        if (whole == 1) {
+            ClusterSync g{cluster_map(&slots[0][0][0], 0), bcast, rank, size, 0u, 0};
+            batched_system(B, sys, g, rank, size, sm, &sflag);
+        } else if (sys >= 0) {
+            BlockSync g{0};
+            batched_system(B, sys, g, 0u, 1u, sm, &sflag);
+        }
+        // every CTA is done with this item (and with CTA 0's slots) before the next claim
+        if (size > 1) cluster_barrier();
+        else __syncthreads();
     }
 }
 

@@ -80,6 +80,10 @@ class PbcgBatch(ctypes.Structure):
                 ("d_rowptr", ctypes.c_void_p), ("d_col", ctypes.c_void_p), ("d_val", ctypes.c_void_p)]
 
 
+class PbcgBatchOpts(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int32), ("pad", ctypes.c_int32), ("cluster_min_rows", ctypes.c_int64)]
+
+
 class PbcgBatchResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("half_step", ctypes.c_int32),
                 ("n_replacements", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
@@ -135,8 +139,8 @@ def lib():
                                             ctypes.POINTER(PbcgMixedInfo)]
         L.pbicgstab_batched_workspace_bytes.argtypes = [ctypes.c_int64]
         L.pbicgstab_batched_workspace_bytes.restype = sz
-        L.pbicgstab_solve_batched.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32, vp,
-                                              sz, vp, vp]
+        L.pbicgstab_solve_batched.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32,
+                                              ctypes.POINTER(PbcgBatchOpts), vp, sz, vp, vp]
         L.pbicgstab_solve_batched.restype = ctypes.c_int
         L.pbicgstab_transpose_work_bytes.argtypes = [i32]
         L.pbicgstab_transpose_work_bytes.restype = sz
@@ -250,10 +254,12 @@ def pbicgstab_batched_workspace_bytes(total_rows: int) -> int:
     return int(lib().pbicgstab_batched_workspace_bytes(int(total_rows)))
 
 
-def pbicgstab_solve_batched(batch: PbcgBatch, total_rows, d_b, d_x, rtol, maxit, replace_period, d_ws, ws_bytes,
-                            d_results, stream) -> int:
+def pbicgstab_solve_batched(batch: PbcgBatch, total_rows, d_b, d_x, rtol, maxit, replace_period, opts, d_ws,
+                            ws_bytes, d_results, stream) -> int:
+    """opts: a PbcgBatchOpts or None (defaults)."""
     return lib().pbicgstab_solve_batched(ctypes.byref(batch), int(total_rows), d_b, d_x, float(rtol), int(maxit),
-                                         int(replace_period), d_ws, int(ws_bytes), d_results, stream)
+                                         int(replace_period), ctypes.byref(opts) if opts is not None else None,
+                                         d_ws, int(ws_bytes), d_results, stream)
 
 
 class BatchSolver:
@@ -281,12 +287,15 @@ class BatchSolver:
                               self.col.data_ptr(), self.val.data_ptr())
         self._np = np
 
-    def launch(self, b, x, rtol=1e-8, maxit=1000, replace_period=0, stream=None):
-        """Enqueue the batched solve (asynchronous)."""
+    def launch(self, b, x, rtol=1e-8, maxit=1000, replace_period=0, stream=None, cluster_size=0,
+               cluster_min_rows=0):
+        """Enqueue the batched solve (asynchronous). cluster_size / cluster_min_rows:
+        the launch shape (0 = library defaults)."""
         torch = self.torch
         st = (stream or torch.cuda.current_stream()).cuda_stream
+        opts = PbcgBatchOpts(int(cluster_size), 0, int(cluster_min_rows))
         rc = pbicgstab_solve_batched(self.desc, self.total, b.data_ptr(), x.data_ptr(), rtol, maxit, replace_period,
-                                     self.ws_ptr, self.ws_bytes, self.results.data_ptr(), st)
+                                     opts, self.ws_ptr, self.ws_bytes, self.results.data_ptr(), st)
         if rc != PBCG_OK:
             raise PbcgError(rc, pbicgstab_last_error())
 

@@ -65,6 +65,7 @@ def test_struct_layouts_match_header(tmp_path):
         "pbcg_coef": native.PbcgCoef, "pbcg_stencil": native.PbcgStencil,
         "pbcg_opts": native.PbcgOpts, "pbcg_info": native.PbcgInfo, "pbcg_mixed_info": native.PbcgMixedInfo,
         "pbcg_batch": native.PbcgBatch, "pbcg_batch_result": native.PbcgBatchResult,
+        "pbcg_batch_opts": native.PbcgBatchOpts,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pbicgstab.h"', "int main(void){"]
     for cname, py in fields.items():

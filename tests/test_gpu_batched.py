@@ -20,15 +20,24 @@ def small_batch():
     return P.random_batch(nsys=24, seed=3, nmin=50, nmax=4000)
 
 
-def test_batched_final_solutions_match_oracle():
+# (cluster_size, cluster_min_rows): every system on one CTA; every system on a
+# whole cluster of 8 or 16 CTAs (min rows 1); large systems on clusters of 4,
+# small ones alone; the library defaults.
+SHAPES = [(1, 0), (8, 1), (16, 1), (4, 1000), (0, 0)]
+SHAPE_IDS = ["alone", "cluster8", "cluster16", "mixed4", "default"]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_batched_final_solutions_match_oracle(shape):
     """Each system solved to rtol 1e-12 (replacement every 20) matches the oracle's
-    solution of that system to 1e-9, and iteration counts agree within 10 %."""
+    solution of that system to 1e-9, and iteration counts agree within 10 %,
+    whether a system is solved by one CTA or by a cluster."""
     import torch
     B = small_batch()
     bs = native.BatchSolver(B)
     b = torch.from_numpy(B.b).cuda()
     x = torch.zeros_like(b)
-    bs.launch(b, x, rtol=1e-12, maxit=3000, replace_period=20)
+    bs.launch(b, x, rtol=1e-12, maxit=3000, replace_period=20, cluster_size=shape[0], cluster_min_rows=shape[1])
     res = bs.fetch_results()
     xg = x.cpu().numpy()
     for s in range(B.nsys):
@@ -43,22 +52,23 @@ def test_batched_final_solutions_match_oracle():
         assert abs(true_rel - res["rel_res_true"][s]) <= 1e-3 * true_rel + 1e-15
 
 
-def test_batched_first_iterations_match_single_system_solver():
-    """A batch of one system takes the same iterations as the single-system
-    oracle, step by step over the first iterations."""
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_batched_iteration_count_matches_oracle(shape):
+    """A batch of one system takes the oracle's number of iterations (within 2)."""
     import torch
     B = P.random_batch(nsys=1, seed=9, nmin=3000, nmax=3000)
     bs = native.BatchSolver(B)
     b = torch.from_numpy(B.b).cuda()
     x = torch.zeros_like(b)
-    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    bs.launch(b, x, rtol=1e-8, maxit=1000, cluster_size=shape[0], cluster_min_rows=shape[1])
     res = bs.fetch_results()
     ref = oracle.pbicgstab(B.system(0), B.b, rtol=1e-8, maxit=1000)
     assert res["status"][0] == native.PBCG_OK
     assert abs(res["iters"][0] - ref.iters) <= 2
 
 
-def test_invalid_system_is_isolated():
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_invalid_system_is_isolated(shape):
     import torch
     B = small_batch()
     col = B.col.copy()
@@ -68,20 +78,24 @@ def test_invalid_system_is_isolated():
     bs = native.BatchSolver(B)
     b = torch.from_numpy(B.b).cuda()
     x = torch.zeros_like(b)
-    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    bs.launch(b, x, rtol=1e-8, maxit=1000, cluster_size=shape[0], cluster_min_rows=shape[1])
     res = bs.fetch_results()
     assert res["status"][5] == native.PBCG_ERR_ARG
     others = np.delete(res["status"], 5)
     assert np.all(others == native.PBCG_OK)
 
 
-def test_batched_launch_replays_in_a_cuda_graph():
+@pytest.mark.parametrize("shape", [(1, 0), (8, 1000)], ids=["alone", "mixed8"])
+def test_batched_launch_replays_in_a_cuda_graph(shape):
+    """A captured launch replays to the bits of a direct launch (the result of a
+    system does not depend on which CTA or cluster took it)."""
     import torch
     B = small_batch()
     bs = native.BatchSolver(B)
     b = torch.from_numpy(B.b).cuda()
     x = torch.zeros_like(b)
-    bs.launch(b, x, rtol=1e-8, maxit=1000)
+    kw = dict(rtol=1e-8, maxit=1000, cluster_size=shape[0], cluster_min_rows=shape[1])
+    bs.launch(b, x, **kw)
     torch.cuda.synchronize()
     direct = x.clone()
     s = torch.cuda.Stream()
@@ -89,9 +103,19 @@ def test_batched_launch_replays_in_a_cuda_graph():
     x.zero_()
     with torch.cuda.graph(g, stream=s):
         x.zero_()
-        bs.launch(b, x, rtol=1e-8, maxit=1000, stream=s)
+        bs.launch(b, x, stream=s, **kw)
     x.fill_(123.0)
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(x, direct)
     assert np.all(bs.fetch_results()["status"] == native.PBCG_OK)
+
+
+def test_unsupported_cluster_size_is_rejected():
+    import torch
+    B = small_batch()
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    with pytest.raises(native.PbcgError):
+        bs.launch(b, x, cluster_size=3)

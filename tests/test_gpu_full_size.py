@@ -19,7 +19,7 @@ N1D = 256
 
 
 @pytest.fixture(scope="module")
-def cfg2():
+def cd3d_256():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -36,8 +36,8 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def test_full_size_spmv_rows(cfg2):
-    st, A, xs, b = cfg2
+def test_full_size_spmv_rows(cd3d_256):
+    st, A, xs, b = cd3d_256
     ss = native.Solver.from_stencil(st)
     sc = native.Solver.from_csr(A)
     xd = dev(xs)
@@ -50,8 +50,8 @@ def test_full_size_spmv_rows(cfg2):
 
 
 @pytest.mark.parametrize("form", ["stencil", "csr"])
-def test_full_size_first_iterations(cfg2, form):
-    st, A, xs, b = cfg2
+def test_full_size_first_iterations(cd3d_256, form):
+    st, A, xs, b = cd3d_256
     k = 10
     ref = oracle.pbicgstab(A, b, rtol=0.0, maxit=k, fixed_iters=k)
     s = native.Solver.from_stencil(st) if form == "stencil" else native.Solver.from_csr(A)
@@ -65,8 +65,8 @@ def test_full_size_first_iterations(cfg2, form):
 
 
 @pytest.mark.parametrize("method,rr", [("pipelined", 50), ("standard", 0)])
-def test_full_size_solve_reaches_tolerance(cfg2, method, rr):
-    st, A, xs, b = cfg2
+def test_full_size_solve_reaches_tolerance(cd3d_256, method, rr):
+    st, A, xs, b = cd3d_256
     s = native.Solver.from_stencil(st)
     x, info = s.solve(dev(b), rtol=1e-8, maxit=5000, replace_period=rr, method=method)
     assert info["status"] == native.PBCG_OK, info

@@ -1,6 +1,6 @@
 """Mixed precision on the GPU: FP64 refinement around FP32 Algorithm 9 (needs a GB300).
 
-Judged by the FP64 oracle: the true residual of the returned x is recomputed by
+Checked by the FP64 oracle: the true residual of the returned x is recomputed by
 the oracle's FP64 SpMV, and the solution is compared with the oracle's FP64
 solution of a tight solve; the error against it is the stated accuracy of the
 mixed-precision result.

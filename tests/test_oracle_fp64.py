@@ -24,7 +24,7 @@ def read_golden(name):
     return out
 
 
-def cfg1():
+def cd2d_64():
     A = P.stencil_to_csr(P.cd2d_constant(64, (10.0, 10.0)))
     xs = P.splitmix64_uniform(0, A.n)
     return A, xs, oracle.spmv(A, xs)
@@ -69,7 +69,7 @@ def test_solution_matches_dense_lu(method, grid):
 def test_bicgstab_matches_scipy_iterates():
     """scipy.sparse.linalg.bicgstab implements the same Algorithm 7 (shadow = r_0,
     x0 = 0); only the dot-product summation order differs."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     scipy_x = []
     spla.bicgstab(scipy_csr(A), b, rtol=1e-30, atol=0.0, maxiter=25, callback=lambda xk: scipy_x.append(xk.copy()))
     res = oracle.bicgstab(A, b, fixed_iters=25, trace=True)
@@ -82,7 +82,7 @@ def test_bicgstab_matches_scipy_iterates():
 def test_pipelined_matches_standard_early_iterations():
     """Exact arithmetic makes Algorithm 7 and Algorithm 9 identical; in FP64 the
     residual norms agree closely in early iterations and drift later (Section 3.3)."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     r7 = oracle.bicgstab(A, b, fixed_iters=20)
     r8 = oracle.cabicgstab(A, b, fixed_iters=20)
     r9 = oracle.pbicgstab(A, b, fixed_iters=20)
@@ -93,7 +93,7 @@ def test_pipelined_matches_standard_early_iterations():
 
 def test_auxiliary_vectors_satisfy_their_definitions():
     """w = A r, s = A p, z = A s, t = A w, v = A z hold up to rounding (Section 3.3)."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     res = oracle.pbicgstab(A, b, fixed_iters=6, keep_work=True)
     W = res.work
     Av = lambda u: oracle.spmv(A, u)
@@ -108,7 +108,7 @@ def test_auxiliary_vectors_satisfy_their_definitions():
 def test_flop_and_vector_counts_match_table1():
     """AXPY + dot-product flops per iteration (Table 1): 20N vs 38N."""
     g = read_golden("table1_costs.txt")
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     n, its = A.n, 10
     r7 = oracle.bicgstab(A, b, fixed_iters=its)
     r9 = oracle.pbicgstab(A, b, fixed_iters=its)
@@ -145,14 +145,14 @@ def test_scaled_identity_converges_in_one_half_step():
 
 
 def test_zero_rhs_returns_immediately():
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     res = oracle.pbicgstab(A, np.zeros(A.n))
     assert res.status == oracle.CONVERGED and res.iters == 0
     assert np.all(res.x == 0.0)
 
 
 def test_nonfinite_input_detected():
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     bad = b.copy()
     bad[7] = np.nan
     res = oracle.pbicgstab(A, bad)
@@ -168,7 +168,7 @@ def true_gap(A, b, res):
 def test_residual_replacement_restores_attainable_accuracy():
     """Section 4.2: without replacement the pipelined method stagnates orders of
     magnitude above BiCGStab; with replacement it reaches BiCGStab's level."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     plain = oracle.bicgstab(A, b, rtol=1e-14, maxit=600)
     pipe = oracle.pbicgstab(A, b, rtol=1e-14, maxit=600)
     assert plain.rel_res_true < 1e-13
@@ -181,7 +181,7 @@ def test_residual_replacement_restores_attainable_accuracy():
 
 
 def test_replacement_cap():
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     rr = oracle.pbicgstab(A, b, rtol=1e-14, maxit=600, replace_period=10, max_replacements=3)
     assert rr.n_replacements == 3
 
@@ -189,7 +189,7 @@ def test_replacement_cap():
 def test_literal_replacement_placement_is_unstable():
     """Replacing r, w, s, z only after p_i, with t_i, rho_i and alpha_i left from the
     recurrences, breaks the Krylov relations; the split placement does not."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     late = oracle.pbicgstab(A, b, rtol=1e-14, maxit=400, replace_period=20, rr_placement=1)
     split = oracle.pbicgstab(A, b, rtol=1e-14, maxit=400, replace_period=20)
     assert not (late.rel_res_true < 1e-6)
@@ -229,7 +229,7 @@ def test_trajectory_sensitivity_to_summation_order():
     magnitude more than 1e-9, while both still converge. This is why iterate-
     by-iterate parity is asserted over the first 20 iterations only, and long
     solves are compared through their final solutions."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
 
     def rdot(u, v):
         return oracle.dot(u[::-1].copy(), v[::-1].copy())

@@ -14,7 +14,7 @@ def bf16_round(v):
     return u.view(np.float32)
 
 
-def cfg1():
+def cd2d_64():
     A = P.stencil_to_csr(P.cd2d_constant(64, (10.0, 10.0)))
     xs = P.splitmix64_uniform(0, A.n)
     return A, xs, oracle.spmv(A, xs)
@@ -26,7 +26,7 @@ def test_bf16_rounding_helper():
 
 
 def test_fp32_inner_solve_reduces_residual_to_inner_tolerance():
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     A32 = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix(
         (A.val.astype(np.float32), A.col, A.rowptr), shape=(A.n, A.n))
     d, its = mixed.pbicgstab_f32(A32, b.astype(np.float32), 1e-4, 1000)
@@ -38,7 +38,7 @@ def test_fp32_inner_solve_reduces_residual_to_inner_tolerance():
 def test_refinement_reaches_1e10_and_matches_fp64_solution():
     """Iterative refinement with an FP32 inner solve reaches an FP64 true residual of
     1e-10, and its solution agrees with the FP64 oracle's to kappa-level accuracy."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     res = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-3)
     assert res["rel_res_true"] <= 1e-10
     assert 2 <= res["outer"] <= 6
@@ -52,7 +52,7 @@ def test_refinement_reaches_1e10_and_matches_fp64_solution():
 def test_fp32_inner_accuracy_limits_each_step():
     """An inner tolerance below what FP32 can attain (~1e-4 here) does not pay:
     inner solves run to their iteration cap, the outer history loses monotonicity."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     tight = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-4, inner_maxit=1000)
     loose = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-3, inner_maxit=1000)
     assert loose["inner_iters"] < tight["inner_iters"]
@@ -61,7 +61,7 @@ def test_fp32_inner_accuracy_limits_each_step():
 def test_refinement_with_exact_values_equals_one_fp64_like_step_count():
     """Inner tolerance 1e-12 with FP32 arithmetic still needs several steps: FP32
     limits each inner solve to about 1e-6 relative accuracy."""
-    A, xs, b = cfg1()
+    A, xs, b = cd2d_64()
     res = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-12, inner_maxit=300)
     assert res["rel_res_true"] <= 1e-10
     assert res["outer"] >= 2

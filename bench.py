@@ -42,9 +42,23 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # Oracle iteration counts on this workload (python -m oracle.full_solve_iterations),
 # used to scale the CPU baseline's per-iteration time to a whole solve.
 ORACLE_ITERS = {"pbicgstab_rr50": 415, "bicgstab": 352}
-# Solver-kernel DRAM traffic per iteration per unknown from an ncu capture of
-# the current kernel source (bytes), or None when not measured for this source.
-TRAFFIC_BYTES_PER_ITER_ROW = None
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the solver kernel on this workload, from a one-pass ncu capture of the full
+# launch (profiles/traffic_pbicgstab_kernel_stencil_cd3d256.md), valid only for
+# the kernel sources it was taken on: SHA-256 over KERNEL_SOURCES.
+KERNEL_SOURCES = ["paper_1612_01395_gb300/csrc/device_common.cuh", "paper_1612_01395_gb300/csrc/operators.cuh",
+                  "paper_1612_01395_gb300/csrc/solvers.cuh"]
+TRAFFIC_CAPTURE = {"bytes_per_launch": 874875431424 + 481760036608, "n": 16777216, "iters": 359, "grid": 912,
+                   "sources_sha256": "3e1e4cb7645460f1d5280080cef220766f13a7211cf0c3ffd03821b60118ff81"}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def parse():
@@ -496,8 +510,10 @@ def run_ours(args):
     bpi = bytes_per_iter(n)
     gbs = bpi * main["iters"] / kern_s / 1e9
     traffic = None
-    if TRAFFIC_BYTES_PER_ITER_ROW is not None:
-        traffic = TRAFFIC_BYTES_PER_ITER_ROW * N * main["iters"]
+    if TRAFFIC_CAPTURE is not None and TRAFFIC_CAPTURE["sources_sha256"] == kernel_sources_sha256() \
+            and TRAFFIC_CAPTURE["n"] == N and TRAFFIC_CAPTURE["iters"] == main["iters"] \
+            and TRAFFIC_CAPTURE["grid"] == infos[0]["grid"]:
+        traffic = TRAFFIC_CAPTURE["bytes_per_launch"]
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "kernel": "pbicgstab_kernel<StencilOp>",

@@ -251,7 +251,7 @@ typedef struct {
 typedef struct {
     int32_t cluster_size;       /* CTAs per cluster: 1 (no clusters), 2, 4, 8 or 16; 0 = 8 */
     int32_t pad;
-    int64_t cluster_min_rows;   /* systems with at least this many rows use a whole cluster; 0 = 8192 */
+    int64_t cluster_min_rows;   /* systems with at least this many rows use a whole cluster; 0 = 512 */
 } pbcg_batch_opts;
 
 /* Workspace of a batched solve: 10 FP64 vectors over all rows + a counter. */

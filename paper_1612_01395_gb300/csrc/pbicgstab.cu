@@ -542,7 +542,7 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
         return fail(PBCG_ERR_OOM, "workspace has %zu bytes, needs %zu", ws_bytes,
                     pbicgstab_batched_workspace_bytes(total_rows));
     int csize = opts && opts->cluster_size ? opts->cluster_size : 8;
-    const long long cmin = opts && opts->cluster_min_rows ? opts->cluster_min_rows : 8192;
+    const long long cmin = opts && opts->cluster_min_rows ? opts->cluster_min_rows : 512;
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)
         return fail(PBCG_ERR_ARG, "cluster_size must be 1, 2, 4, 8 or 16 (got %d)", csize);
     if (cmin < 0) return fail(PBCG_ERR_ARG, "cluster_min_rows must be >= 0");

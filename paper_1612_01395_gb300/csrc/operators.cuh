@@ -64,17 +64,45 @@ struct CsrOpT {
         using T = decltype(u(0));
         const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
         T acc = T(0);
-        for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(__ldg(col + k)), acc);
+        if constexpr (sizeof(V) >= 8) {
+            for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(__ldg(col + k)), acc);
+        } else {
+            // Low-precision values (the FP32 inner solves): a sweep is bound by
+            // memory latency, not arithmetic, so the entries of a row are taken
+            // kW at a time -- all column indices and values in flight together,
+            // then all gathers, then the FMAs in storage order (the same sum as
+            // the one-by-one loop).
+            constexpr int kW = 8;
+            for (int k0 = b; k0 < e; k0 += kW) {
+                int c[kW] = {};
+                V v[kW] = {};
+                T xv[kW] = {};
+#pragma unroll
+                for (int j = 0; j < kW; ++j)
+                    if (k0 + j < e) {
+                        c[j] = __ldg(col + k0 + j);
+                        v[j] = __ldg(val + k0 + j);
+                    }
+#pragma unroll
+                for (int j = 0; j < kW; ++j)
+                    if (k0 + j < e) xv[j] = u(c[j]);
+#pragma unroll
+                for (int j = 0; j < kW; ++j)
+                    if (k0 + j < e) acc = fmaT(value_as<T>(v[j]), xv[j], acc);
+            }
+        }
         return acc;
     }
 };
 using CsrOp = CsrOpT<double>;
 
 // One coefficient: t1[i*a1 + j*b1 + k*c1] (or `value` when t1 is null) plus
-// t2[i*a2 + j*b2 + k*c2] when t2 is set. Indices fit 31 bits (checked at create).
+// t2[i*a2 + j*b2 + k*c2] when t2 is set (n2 = 1, else 0). Indices fit 31 bits
+// (checked at create).
 struct StCoef {
     const double *t1, *t2;
     int a1, b1, c1, a2, b2, c2;
+    int n2;
     double value;
 };
 
@@ -87,7 +115,15 @@ struct StencilOp {
     __device__ __forceinline__ double coef(int d, int i, int j, int k) const {
         const StCoef &q = c[d];
         double v = q.t1 ? __ldg(q.t1 + (i * q.a1 + j * q.b1 + k * q.c1)) : q.value;
-        if (q.t2) v = __dadd_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
+        // The second table is rare (a coefficient varying along two separate
+        // directions), and its addition is written as a loop of n2 (0 or 1)
+        // trips so that the compiler jumps over it rather than predicating it:
+        // a DADD whose lanes are all predicated off still occupies the FP64
+        // pipe for a whole warp instruction (64 cycles per sub-partition on
+        // this GPU), which as an if-converted branch cost 6 dead DADDs per row
+        // of a 7-point stencil with one summed coefficient.
+#pragma unroll 1
+        for (int m = 0; m < q.n2; ++m) v = __dadd_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
         return v;
     }
 

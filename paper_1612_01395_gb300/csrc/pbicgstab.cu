@@ -350,6 +350,7 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
             q.a2 = c.data2 ? (int)c.stride2[0] : 0;
             q.b2 = c.data2 ? (int)c.stride2[1] : 0;
             q.c2 = c.data2 ? (int)c.stride2[2] : 0;
+            q.n2 = c.data2 ? 1 : 0;
             q.value = c.value;
             o.c[d] = q;
         }

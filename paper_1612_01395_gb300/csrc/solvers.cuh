@@ -184,6 +184,13 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     const VectorsT<T> &V = a.V;
     T *x = a.x;
     const bool fixed = a.fixed != 0;
+    // Rows per step of the two main sweeps. A step loads all its rows before
+    // storing any: the stores of one row may alias the loads of the next as
+    // far as the compiler knows, so with one row per step each row waits for
+    // the previous row's loads. FP32 sweeps (the inner solves) are bound by
+    // that latency and take two rows per step; FP64 sweeps are bound by the
+    // FP64 pipe and keep one. Rows are accumulated in the same order either way.
+    constexpr int kRows = sizeof(T) == 4 ? 2 : 1;
 
     // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
     double d0[1];
@@ -233,26 +240,45 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         DotAcc<T> a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         const T al = (T)alpha, be = (T)beta, om = (T)omega;
         if (!replaced_rw) {
-            PBCG_ROWS(i) {
-                const T ti = A.row(i, VecLoadT<T>{V.w});
-                const T ri = V.r[i], wi = V.w[i], si = V.s[i], zi = V.z[i];
-                const T pn = fmaT(be, fmaT(-om, si, V.p[i]), ri);   // p_i
-                const T sn = fmaT(be, fmaT(-om, zi, si), wi);       // s_i, eq. (1)
-                const T zn = fmaT(be, fmaT(-om, V.v[i], zi), ti);   // z_i, eq. (6)
-                const T qi = fmaT(-al, sn, ri);                     // q_i
-                const T yi = fmaT(-al, zn, wi);                     // y_i, eq. (4)
-                V.t[i] = ti;
-                V.p[i] = pn;
-                V.s[i] = sn;
-                V.z[i] = zn;
-                V.q[i] = qi;
-                V.y[i] = yi;
-                const T r0i = V.r0[i];
-                a1[0].add(qi, yi);
-                a1[1].add(yi, yi);
-                a1[2].add(qi, qi);
-                a1[3].add(r0i, sn);
-                a1[4].add(r0i, zn);
+            for (int i0 = lo + (int)threadIdx.x; i0 < hi; i0 += kRows * kTPB) {
+                T ti[kRows] = {}, ri[kRows] = {}, wi[kRows] = {}, si[kRows] = {}, zi[kRows] = {}, pi[kRows] = {},
+                  vi[kRows] = {}, r0i[kRows] = {};
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int i = i0 + u * kTPB;
+                    if (i < hi) {
+                        ti[u] = A.row(i, VecLoadT<T>{V.w});
+                        ri[u] = V.r[i];
+                        wi[u] = V.w[i];
+                        si[u] = V.s[i];
+                        zi[u] = V.z[i];
+                        pi[u] = V.p[i];
+                        vi[u] = V.v[i];
+                        r0i[u] = V.r0[i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int i = i0 + u * kTPB;
+                    if (i < hi) {
+                        const T pn = fmaT(be, fmaT(-om, si[u], pi[u]), ri[u]);   // p_i
+                        const T sn = fmaT(be, fmaT(-om, zi[u], si[u]), wi[u]);   // s_i, eq. (1)
+                        const T zn = fmaT(be, fmaT(-om, vi[u], zi[u]), ti[u]);   // z_i, eq. (6)
+                        const T qi = fmaT(-al, sn, ri[u]);                       // q_i
+                        const T yi = fmaT(-al, zn, wi[u]);                       // y_i, eq. (4)
+                        V.t[i] = ti[u];
+                        V.p[i] = pn;
+                        V.s[i] = sn;
+                        V.z[i] = zn;
+                        V.q[i] = qi;
+                        V.y[i] = yi;
+                        a1[0].add(qi, yi);
+                        a1[1].add(yi, yi);
+                        a1[2].add(qi, qi);
+                        a1[3].add(r0i[u], sn);
+                        a1[4].add(r0i[u], zn);
+                    }
+                }
             }
             ++spmvs;
         } else {
@@ -307,19 +333,37 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         DotAcc<T> a2[3];   // (r0,r) (r0,w) (r,r)
         const T om2 = (T)omega;
         if (!replace_now) {
-            PBCG_ROWS(i) {
-                const T vi = A.row(i, VecLoadT<T>{V.z});
-                const T qi = V.q[i], yi = V.y[i];
-                x[i] = fmaT(om2, qi, fmaT(al, V.p[i], x[i]));
-                const T rn = fmaT(-om2, yi, qi);                        // eq. (7)
-                const T wn = fmaT(-om2, fmaT(-al, vi, V.t[i]), yi);     // eq. (8)
-                V.v[i] = vi;
-                V.r[i] = rn;
-                V.w[i] = wn;
-                const T r0i = V.r0[i];
-                a2[0].add(r0i, rn);
-                a2[1].add(r0i, wn);
-                a2[2].add(rn, rn);
+            for (int i0 = lo + (int)threadIdx.x; i0 < hi; i0 += kRows * kTPB) {
+                T vi[kRows] = {}, qi[kRows] = {}, yi[kRows] = {}, xi[kRows] = {}, pi[kRows] = {}, ti[kRows] = {},
+                  r0i[kRows] = {};
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int i = i0 + u * kTPB;
+                    if (i < hi) {
+                        vi[u] = A.row(i, VecLoadT<T>{V.z});
+                        qi[u] = V.q[i];
+                        yi[u] = V.y[i];
+                        xi[u] = x[i];
+                        pi[u] = V.p[i];
+                        ti[u] = V.t[i];
+                        r0i[u] = V.r0[i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRows; ++u) {
+                    const int i = i0 + u * kTPB;
+                    if (i < hi) {
+                        x[i] = fmaT(om2, qi[u], fmaT(al, pi[u], xi[u]));
+                        const T rn = fmaT(-om2, yi[u], qi[u]);                          // eq. (7)
+                        const T wn = fmaT(-om2, fmaT(-al, vi[u], ti[u]), yi[u]);        // eq. (8)
+                        V.v[i] = vi[u];
+                        V.r[i] = rn;
+                        V.w[i] = wn;
+                        a2[0].add(r0i[u], rn);
+                        a2[1].add(r0i[u], wn);
+                        a2[2].add(rn, rn);
+                    }
+                }
             }
             ++spmvs;
         } else {
@@ -1065,7 +1109,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
     if (part == 0 && threadIdx.x == 0) B.out[sys] = res;
 }
 
-__global__ void __launch_bounds__(kTPB) batched_kernel(const BatchArgs B) {
+__global__ void __launch_bounds__(kTPB, 6) batched_kernel(const BatchArgs B) {
     __shared__ double sm[kMaxDots][32];
     __shared__ double slots[2][kMaxCluster][kSlotDoubles];   // used in CTA 0 of a cluster
     __shared__ double bcast[kMaxDots];

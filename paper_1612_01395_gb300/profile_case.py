@@ -8,6 +8,9 @@ so a profiler can skip the warm-up launch and capture the next one:
 
 Problems: cd3d (3-D convection-diffusion, velocity (20 sin y, 20 cos z, 20 sin x),
 n^3 grid), cd2d (2-D, constant velocity (10, 10), n^2 grid).
+
+--method mixed (CSR form only) runs one refinement step whose FP32 inner
+solve takes exactly --iters iterations (FP32 values; --bf16 for BF16 values).
 """
 import argparse
 import json
@@ -22,7 +25,8 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--iters", type=int, default=5, help="fixed iterations per solve (0: solve to --rtol)")
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--method", default="pipelined", choices=["pipelined", "standard"])
+    ap.add_argument("--method", default="pipelined", choices=["pipelined", "standard", "mixed"])
+    ap.add_argument("--bf16", action="store_true", help="BF16 values for --method mixed")
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--form", default="stencil", choices=["stencil", "csr"])
     ap.add_argument("--replace-period", type=int, default=0)
@@ -37,6 +41,24 @@ def main(argv=None):
     s = native.Solver.from_stencil(st) if args.form == "stencil" else native.Solver.from_csr(P.stencil_to_csr(st))
     xs = torch.from_numpy(P.splitmix64_uniform(0, st.n)).cuda()
     b = s.spmv(xs)
+    if args.method == "mixed":
+        if args.form != "csr":
+            raise SystemExit("--method mixed needs --form csr")
+        A = P.stencil_to_csr(st)
+        lowp = torch.as_tensor(A.val).cuda().to(torch.bfloat16 if args.bf16 else torch.float32)
+        typ = native.PBCG_VALUES_BF16 if args.bf16 else native.PBCG_VALUES_F32
+        mk = dict(rtol=0.0, max_outer=1, inner_rtol=0.0, inner_maxit=args.iters, grid=args.grid)
+        s.solve_mixed(b, lowp, typ, **mk)   # warm-up launch
+        out = [s.solve_mixed(b, lowp, typ, **mk)[1] for _ in range(args.repeat)]
+        torch.cuda.synchronize()
+        ms = [i["kernel_ms"] for i in out]
+        its = out[0]["inner_iters"]
+        print(json.dumps({"problem": args.problem, "n": st.n, "form": args.form, "method": args.method,
+                          "values": "bf16" if args.bf16 else "fp32", "inner_iters": its,
+                          "kernel_ms": float(np.median(ms)), "us_per_iter": 1e3 * float(np.median(ms)) / max(its, 1),
+                          "grid": out[0]["grid"], "grid_syncs": out[0]["grid_syncs"], "status": out[0]["status"]}))
+        s.close()
+        return 0
     kw = dict(method=args.method, plain_variant=args.variant, grid=args.grid, replace_period=args.replace_period)
     if args.iters > 0:
         kw.update(rtol=0.0, maxit=args.iters, fixed_iters=args.iters)

@@ -222,6 +222,33 @@ def test_ptp1_iteration_count_in_paper_range():
     assert lo <= res.iters <= hi
 
 
+@pytest.mark.slow
+def test_ptp1_attainable_accuracy_matches_paper():
+    """PTP1 accuracy experiment (Section 5, Figure 4): true residual norms the
+    paper reports as attained within 2000 iterations -- BiCGStab 5.8e-12,
+    p-BiCGStab 1.7e-9, p-BiCGStab-rr (every 100 iterations, at most 10) 2.5e-12.
+    Another reduction order (the paper ran on 240 processes) changes these
+    levels, so the pin is the order of magnitude (factor 10) and the ordering:
+    without replacement the pipelined method stalls two to three orders above
+    the other two. p-BiCGStab is sampled at its best region (the true residual
+    grows again after it): fixed 500 iterations."""
+    g = read_golden("ptp_reference.txt")
+    A = P.stencil_to_csr(P.ptp1(1000))
+    b = oracle.spmv(A, np.ones(A.n))
+
+    def true_res(x):
+        return np.linalg.norm(b - oracle.spmv(A, x))
+
+    std = true_res(oracle.bicgstab(A, b, rtol=1e-17, maxit=2000).x)
+    rr = true_res(oracle.pbicgstab(A, b, rtol=1e-17, maxit=2000, replace_period=100, max_replacements=10).x)
+    pipe = true_res(oracle.pbicgstab(A, b, rtol=0.0, maxit=500, fixed_iters=500).x)
+    for got, key in ((std, "ptp1_attained_bicgstab"), (rr, "ptp1_attained_pbicgstab_rr"),
+                     (pipe, "ptp1_attained_pbicgstab")):
+        paper = float(g[key][0])
+        assert paper / 10 <= got <= paper * 10, (key, got)
+    assert pipe > 100 * max(std, rr)
+
+
 def test_trajectory_sensitivity_to_summation_order():
     """Two equally valid FP64 evaluations of Algorithm 9 -- dot products summed
     left to right (the oracle) or right to left -- agree closely for ~20

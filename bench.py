@@ -48,8 +48,8 @@ ORACLE_ITERS = {"pbicgstab_rr50": 415, "bicgstab": 352}
 # the kernel sources it was taken on: SHA-256 over KERNEL_SOURCES.
 KERNEL_SOURCES = ["paper_1612_01395_gb300/csrc/device_common.cuh", "paper_1612_01395_gb300/csrc/operators.cuh",
                   "paper_1612_01395_gb300/csrc/solvers.cuh"]
-TRAFFIC_CAPTURE = {"bytes_per_launch": 874875431424 + 481760036608, "n": 16777216, "iters": 359, "grid": 912,
-                   "sources_sha256": "3e1e4cb7645460f1d5280080cef220766f13a7211cf0c3ffd03821b60118ff81"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 984085750016 + 539634942720, "n": 16777216, "iters": 402, "grid": 1216,
+                   "sources_sha256": "bbe003a3535f829374b76b350c994a7f078832a657045a4a53318e3a8687a8dc"}
 
 
 def kernel_sources_sha256():
@@ -274,6 +274,28 @@ def timed_solves(solver, bd, x, steps, method, rr, barrier):
     torch.cuda.synchronize()
     barrier()
     return e0.elapsed_time(e1) / 1e3, infos
+
+
+def grid_sensitivity(solver, bd, x, grid):
+    """Iterations to rtol of both methods at other grid sizes. The grid fixes
+    the order in which dot products are summed, and BiCGStab's trajectory
+    depends on rounding: the counts to 1e-8 move by 10-20 %, so the time
+    comparison of the two methods is also given per iteration."""
+    from paper_1612_01395_gb300 import native
+    out = {}
+    for g in sorted({grid // 2, (3 * grid) // 4, grid}):
+        row = {}
+        for method in ("pipelined", "standard"):
+            x.zero_()
+            if method == "pipelined":
+                st, info = native.pbicgstab_solve(solver.h, bd.data_ptr(), x.data_ptr(), RTOL, MAXIT, REPLACE_PERIOD,
+                                                  grid=g)
+            else:
+                st, info = native.bicgstab_solve(solver.h, bd.data_ptr(), x.data_ptr(), RTOL, MAXIT, grid=g)
+            row[method] = {"iters": info.iters, "ms_per_iter": info.kernel_ms / max(info.iters, 1),
+                           "status": native.STATUS_NAMES.get(st)}
+        out[str(g)] = row
+    return out
 
 
 def summarize(elapsed, infos, steps):
@@ -549,6 +571,7 @@ def run_ours(args):
             cmp_csr["pbicgstab" if method == "pipelined" else "bicgstab"] = r
         out["csr"] = cmp_csr
         csolver.close()
+        out["grid_sensitivity"] = grid_sensitivity(solver, bd, x, main["grid"])
 
     if not args.no_mixed:
         out["mixed_precision"] = mixed_precision_case(args.mixed_n, args.steps, barrier)

@@ -50,16 +50,13 @@ struct SolveArgsT {
 using SolveArgs = SolveArgsT<double>;
 
 // Resident blocks per SM the solver kernels are compiled for (register cap
-// 65536 / (kTPB * kMinBlocks)): the large-n sweeps are limited by the FP64 pipe,
-// which needs many warps in flight to cover memory latency. The stencil's
-// coefficient evaluation needs a little more registers than CSR.
+// 65536 / (kTPB * kMinBlocks) = 64): the large-n sweeps are limited by the
+// FP64 pipe, which needs many warps in flight to cover memory latency. At
+// 256^3 the stencil kernels take 1.25 (p-BiCGStab) and 1.27 ms (BiCGStab) per
+// iteration with 6 blocks per SM and 1.18 and 1.10 ms with 8; neither spills.
 template <class Op>
 struct Tune {
     static constexpr int kMinBlocks = 8;
-};
-template <>
-struct Tune<StencilOp> {
-    static constexpr int kMinBlocks = 6;
 };
 
 struct Outcome {

@@ -298,6 +298,16 @@ pbcg_status pbicgstab_csr_transpose(int32_t n, int32_t nnz, const int32_t *d_row
 pbcg_status pbicgstab_csr_value_grad(int32_t n, const int32_t *d_rowptr, const int32_t *d_col,
                                      const double *d_lambda, const double *d_x, double *d_grad, void *stream);
 
+/* Diagnostic of failure detection (no counterpart in the paper): runs, on
+ * h's stream and workspace, a two-block grid synchronisation that one block
+ * never joins, with each wait bounded by limit_ms (1..4000). The wait must end
+ * at its limit; *status receives the status the device recorded
+ * (PBCG_ERR_TIMEOUT when the bound works; PBCG_OK would mean the wait was not
+ * bounded). Returns PBCG_ERR_ARG / PBCG_ERR_CUDA for bad arguments or a failed
+ * launch, else PBCG_OK. The handle stays usable. Blocks the calling thread
+ * until the probe ends. */
+pbcg_status pbicgstab_probe_sync_timeout(pbicgstab_t h, int32_t limit_ms, int32_t *status);
+
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
 #define PBCG_NOALLOC_MAX_N 32768
 

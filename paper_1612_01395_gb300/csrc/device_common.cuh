@@ -139,8 +139,8 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double (*sm)[32]) {
 // all slots from every thread congests the L2 and was measured slower. The
 // rotation keeps a slot from being rewritten while a slow block may still read
 // it (a block writes exchange e+3 only after all blocks arrived at e+2, i.e.
-// after all finished reading exchange e). Every wait is bounded
-// (kSyncTimeoutNs) and watches the abort flag.
+// after all finished reading exchange e). Every wait is bounded (limit_ns,
+// kSyncTimeoutNs by default) and watches the abort flag.
 constexpr int kSlotDoubles = 8;
 
 struct GridSync {
@@ -148,6 +148,7 @@ struct GridSync {
     double *slots;      // [3][gridDim.x][kSlotDoubles]
     unsigned epoch;     // exchanges done by this block
     int count;          // exchanges performed (for diagnostics)
+    uint64_t limit_ns = kSyncTimeoutNs;   // bound on each wait
 };
 
 __device__ __forceinline__ double *slot_ptr(const GridSync &g, unsigned buf, int block) {
@@ -169,7 +170,7 @@ __device__ __forceinline__ bool exchange(GridSync &g, const double (&mine)[K], d
         const uint64_t t0 = globaltimer_ns();
         while (ld_acquire_u32(&g.ctl->arrivals) < target) {
             if (ld_relaxed_s32(&g.ctl->abort) != 0) { *sflag = 0; break; }
-            if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
+            if (globaltimer_ns() - t0 > g.limit_ns) {
                 atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
                 *sflag = 0;
                 break;

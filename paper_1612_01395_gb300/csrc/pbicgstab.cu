@@ -519,6 +519,27 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
 }
 
 // ---------------------------------------------------------------------------
+// Diagnostic of the bounded grid-wide wait.
+// ---------------------------------------------------------------------------
+extern "C" pbcg_status pbicgstab_probe_sync_timeout(pbicgstab_t h, int32_t limit_ms, int32_t *status) {
+    if (!h || !status) return fail(PBCG_ERR_ARG, "handle or status is NULL");
+    if (limit_ms < 1 || limit_ms > 4000) return fail(PBCG_ERR_ARG, "limit_ms must be in [1, 4000]");
+    *status = PBCG_OK;
+    PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
+    pbcg::Control *ctl = h->ctl;
+    double *slots = h->partials;
+    uint64_t limit_ns = (uint64_t)limit_ms * 1000000ull;
+    void *args[] = {&ctl, &slots, &limit_ns};
+    PBCG_CUDA(cudaLaunchCooperativeKernel((const void *)pbcg::sync_timeout_probe_kernel, dim3(2), dim3(pbcg::kTPB),
+                                          args, 0, h->stream));
+    pbcg::Control c;
+    PBCG_CUDA(cudaMemcpyAsync(&c, h->ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    PBCG_CUDA(cudaStreamSynchronize(h->stream));
+    *status = c.status;
+    return PBCG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched solves.
 // ---------------------------------------------------------------------------
 extern "C" size_t pbicgstab_batched_workspace_bytes(int64_t total_rows) {

@@ -1156,6 +1156,20 @@ __global__ void __launch_bounds__(kTPB, 6) batched_kernel(const BatchArgs B) {
     }
 }
 
+// Diagnostic of the bounded grid-wide wait: every block but the last enters a
+// grid synchronisation that the last block never joins, so the wait cannot
+// complete and must end at its limit. The first block to give up records
+// PBCG_ERR_TIMEOUT in the abort flag; the others see the flag (or their own
+// limit) and return. Block 0 then reports the flag.
+__global__ void sync_timeout_probe_kernel(Control *ctl, double *slots, uint64_t limit_ns) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ int sflag;
+    if (blockIdx.x == gridDim.x - 1) return;
+    GridSync g{ctl, slots, 0u, 0, limit_ns};
+    const bool ok = grid_sync(g, sm, &sflag);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->status = ok ? (int)PBCG_OK : ld_relaxed_s32(&ctl->abort);
+}
+
 // y = A x, one row per thread, grid-stride.
 template <class Op>
 __global__ void __launch_bounds__(kTPB) spmv_kernel(const Op A, const double *x, double *y) {

@@ -32,7 +32,8 @@ EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_workspace_bytes_prec", "pbicg
            "pbicgstab_solve", "bicgstab_solve", "pbicgstab_solve_host", "pbicgstab_spmv",
            "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
            "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched",
-           "pbicgstab_transpose_work_bytes", "pbicgstab_csr_transpose", "pbicgstab_csr_value_grad"]
+           "pbicgstab_transpose_work_bytes", "pbicgstab_csr_transpose", "pbicgstab_csr_value_grad",
+           "pbicgstab_probe_sync_timeout"]
 PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
@@ -147,6 +148,8 @@ def lib():
         L.pbicgstab_csr_transpose.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         L.pbicgstab_csr_transpose.restype = ctypes.c_int
         L.pbicgstab_csr_value_grad.argtypes = [i32, vp, vp, vp, vp, vp, vp]
+        L.pbicgstab_probe_sync_timeout.argtypes = [vp, i32, ctypes.POINTER(i32)]
+        L.pbicgstab_probe_sync_timeout.restype = ctypes.c_int
         L.pbicgstab_csr_value_grad.restype = ctypes.c_int
         L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
                                                   ctypes.POINTER(PbcgOpts), vp, ctypes.POINTER(PbcgInfo)]
@@ -321,6 +324,13 @@ def pbicgstab_csr_transpose(n, nnz, d_rowptr, d_col, d_val, d_trowptr, d_tcol, d
 
 def pbicgstab_csr_value_grad(n, d_rowptr, d_col, d_lambda, d_x, d_grad, stream) -> int:
     return lib().pbicgstab_csr_value_grad(int(n), d_rowptr, d_col, d_lambda, d_x, d_grad, stream)
+
+
+def pbicgstab_probe_sync_timeout(h, limit_ms):
+    """Returns (call status, status the device recorded)."""
+    st = ctypes.c_int32(-1)
+    rc = lib().pbicgstab_probe_sync_timeout(h, int(limit_ms), ctypes.byref(st))
+    return rc, st.value
 
 
 def pbicgstab_spmv(h, d_x, d_y) -> int:

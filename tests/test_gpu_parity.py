@@ -290,3 +290,21 @@ def test_create_rejects_bad_input():
     x = dev(np.ones(A.n))
     assert native.pbicgstab_spmv(h, x.data_ptr(), x.data_ptr() + 8) == native.PBCG_ERR_ARG
     native.pbicgstab_destroy(h)
+
+
+def test_bounded_grid_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a grid synchronisation that one block
+    never joins ends at its bound (0.2 s) with PBCG_ERR_TIMEOUT recorded on the
+    device and read by the host; the same handle then solves normally."""
+    import time
+    s, A = solver_for("cd2d_64", "csr")
+    t0 = time.perf_counter()
+    rc, st = native.pbicgstab_probe_sync_timeout(s.h, 200)
+    dt = time.perf_counter() - t0
+    assert rc == native.PBCG_OK
+    assert st == native.PBCG_ERR_TIMEOUT
+    assert 0.2 <= dt < 10.0
+    b = dev(oracle.spmv(A, P.splitmix64_uniform(0, A.n)))
+    x, info = s.solve(b, rtol=1e-8, maxit=1000)
+    assert info["status"] == native.PBCG_OK
+    s.close()

@@ -311,7 +311,7 @@ def summarize(elapsed, infos, steps):
 def mixed_precision_case(n, steps, barrier):
     """FP64 refinement around FP32 (and BF16-valued) Algorithm 9 against all-FP64
     p-BiCGStab, both to a true relative residual of 1e-10, on the n^3
-    convection-diffusion system in CSR form."""
+    convection-diffusion system in CSR form and in stencil form."""
     import torch
     from paper_1612_01395_gb300 import native, problems as P
     st = P.cd3d_trig(n)
@@ -321,7 +321,8 @@ def mixed_precision_case(n, steps, barrier):
     bd = s.spmv(torch.from_numpy(P.splitmix64_uniform(SEED, N)).cuda())
     v32 = torch.as_tensor(A.val).cuda().to(torch.float32)
     v16 = torch.as_tensor(A.val).cuda().to(torch.bfloat16)
-    out = {"workload": f"3-D convection-diffusion {n}^3 (n={N}), CSR (nnz={A.nnz}), true rel.res 1e-10"}
+    out = {"workload": f"3-D convection-diffusion {n}^3 (n={N}), CSR (nnz={A.nnz}) and stencil forms, "
+                       f"true rel.res 1e-10"}
     runs = {}
 
     def timed(fn, k):
@@ -359,6 +360,22 @@ def mixed_precision_case(n, steps, barrier):
                       "rel_error_vs_fp64": err, "speedup_vs_fp64": runs["fp64_pbicgstab"]["value"] / sec,
                       "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
     s.close()
+    # stencil form: no matrix bytes; the inner solves use the coefficient tables rounded to FP32
+    ss = native.Solver.from_stencil(st)
+    sec, (x64s, i64s) = timed(lambda: ss.solve(bd, rtol=1e-10, maxit=MAXIT, replace_period=REPLACE_PERIOD), k)
+    runs["stencil_fp64_pbicgstab"] = {"value": sec, "iters": i64s["iters"], "rel_res_true": i64s["rel_res_true"],
+                                      "status": native.STATUS_NAMES[i64s["status"]]}
+    for tau in (1e-1, 1e-2):
+        sec, (xm, im) = timed(lambda: ss.solve_mixed(bd, None, native.PBCG_VALUES_F32, rtol=1e-10, max_outer=40,
+                                                     inner_rtol=tau, inner_maxit=INNER_MAXIT), k)
+        err = float(torch.linalg.norm(xm - x64s) / torch.linalg.norm(x64s))
+        inner_bytes = 24 * 4 * N   # FP32 vectors only, per inner iteration
+        runs[f"stencil_mixed_fp32_inner{tau:g}"] = {
+            "value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"], "inner_maxit": INNER_MAXIT,
+            "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
+            "rel_error_vs_fp64": err, "speedup_vs_fp64_stencil": runs["stencil_fp64_pbicgstab"]["value"] / sec,
+            "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
+    ss.close()
     out.update(runs)
     return out
 

@@ -205,15 +205,21 @@ enum { PBCG_VALUES_F32 = 0, PBCG_VALUES_BF16 = 1 };
 /* Mixed-precision solve (an extension of the paper's method, which states no
  * precision): FP64 iterative refinement around pipelined BiCGStab
  * (Algorithm 9) run on FP32 vectors. Each step computes r = b - A x with the
- * handle's FP64 CSR matrix, solves A d = r with the FP32 pipelined iteration
- * to ||r_inner|| <= inner_rtol ||r|| (at most inner_maxit iterations) on the
- * low-precision copy of A's values, and sets x := x + d in FP64. Dot products
- * that set alpha, beta and omega are accumulated in FP64. Stops when the FP64
- * residual satisfies ||b - A x|| <= rtol ||b - A x0|| or after max_outer steps
+ * handle's FP64 operator, solves A d = r with the FP32 pipelined iteration
+ * to ||r_inner|| <= inner_rtol ||r|| (at most inner_maxit iterations) on a
+ * low-precision copy of A, and sets x := x + d in FP64. Dot products that set
+ * alpha, beta and omega are accumulated to FP64 accuracy (compensated FP32
+ * per thread, FP64 across threads). Stops when the FP64 residual satisfies
+ * ||b - A x|| <= rtol ||b - A x0|| or after max_outer steps
  * (PBCG_NOT_CONVERGED).
- *   h            a CSR handle (PBCG_ERR_ARG for a stencil handle)
- *   d_val_lowp   nnz values of the same CSR structure as float
- *                (PBCG_VALUES_F32) or bfloat16 (PBCG_VALUES_BF16), caller-owned
+ *   h            a CSR or stencil handle
+ *   d_val_lowp   CSR handle: nnz values of the same CSR structure as float
+ *                (PBCG_VALUES_F32) or bfloat16 (PBCG_VALUES_BF16),
+ *                caller-owned. Stencil handle: NULL with PBCG_VALUES_F32; the
+ *                library rounds the coefficient tables to FP32 into the
+ *                workspace each call (PBCG_ERR_ARG if they need more than the
+ *                12 * round32(n) floats the inner vectors leave free, or for
+ *                other arguments)
  *   opts         NULL or options; d_history (max_outer + 1 doubles) receives
  *                the FP64 residual norm before each step; grid as for solve
  * Uses the handle's workspace (no extra memory). */

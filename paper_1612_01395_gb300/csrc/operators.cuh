@@ -98,23 +98,30 @@ using CsrOp = CsrOpT<double>;
 
 // One coefficient: t1[i*a1 + j*b1 + k*c1] (or `value` when t1 is null) plus
 // t2[i*a2 + j*b2 + k*c2] when t2 is set (n2 = 1, else 0). Indices fit 31 bits
-// (checked at create).
-struct StCoef {
-    const double *t1, *t2;
+// (checked at create). C is the type of the tables: double, or float for the
+// low-precision inner solves (tables rounded to FP32 by the library).
+template <typename C>
+struct StCoefT {
+    const C *t1, *t2;
     int a1, b1, c1, a2, b2, c2;
     int n2;
-    double value;
+    C value;
 };
+using StCoef = StCoefT<double>;
 
-struct StencilOp {
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+template <typename C>
+struct StencilOpT {
     int n, nx, ny, nz;
     int nxy;
     FastDiv dx, dy;
-    StCoef c[7];   // C, W, E, S, N, B, T
+    StCoefT<C> c[7];   // C, W, E, S, N, B, T
 
-    __device__ __forceinline__ double coef(int d, int i, int j, int k) const {
-        const StCoef &q = c[d];
-        double v = q.t1 ? __ldg(q.t1 + (i * q.a1 + j * q.b1 + k * q.c1)) : q.value;
+    __device__ __forceinline__ C coef(int d, int i, int j, int k) const {
+        const StCoefT<C> &q = c[d];
+        C v = q.t1 ? __ldg(q.t1 + (i * q.a1 + j * q.b1 + k * q.c1)) : q.value;
         // The second table is rare (a coefficient varying along two separate
         // directions), and its addition is written as a loop of n2 (0 or 1)
         // trips so that the compiler jumps over it rather than predicating it:
@@ -123,26 +130,28 @@ struct StencilOp {
         // this GPU), which as an if-converted branch cost 6 dead DADDs per row
         // of a 7-point stencil with one summed coefficient.
 #pragma unroll 1
-        for (int m = 0; m < q.n2; ++m) v = __dadd_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
+        for (int m = 0; m < q.n2; ++m) v = add_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
         return v;
     }
 
     template <class L>
-    __device__ __forceinline__ double row(int r, const L &u) const {
+    __device__ __forceinline__ auto row(int r, const L &u) const -> decltype(u(0)) {
+        using T = decltype(u(0));
         const int t = (int)dx.div((uint32_t)r);
         const int i = r - t * nx;
         const int k = (int)dy.div((uint32_t)t);
         const int j = t - k * ny;
-        double acc = 0.0;
-        if (k > 0) acc = fma(coef(PBCG_B, i, j, k), u(r - nxy), acc);
-        if (j > 0) acc = fma(coef(PBCG_S, i, j, k), u(r - nx), acc);
-        if (i > 0) acc = fma(coef(PBCG_W, i, j, k), u(r - 1), acc);
-        acc = fma(coef(PBCG_C, i, j, k), u(r), acc);
-        if (i < nx - 1) acc = fma(coef(PBCG_E, i, j, k), u(r + 1), acc);
-        if (j < ny - 1) acc = fma(coef(PBCG_N, i, j, k), u(r + nx), acc);
-        if (k < nz - 1) acc = fma(coef(PBCG_T, i, j, k), u(r + nxy), acc);
+        T acc = T(0);
+        if (k > 0) acc = fmaT((T)coef(PBCG_B, i, j, k), u(r - nxy), acc);
+        if (j > 0) acc = fmaT((T)coef(PBCG_S, i, j, k), u(r - nx), acc);
+        if (i > 0) acc = fmaT((T)coef(PBCG_W, i, j, k), u(r - 1), acc);
+        acc = fmaT((T)coef(PBCG_C, i, j, k), u(r), acc);
+        if (i < nx - 1) acc = fmaT((T)coef(PBCG_E, i, j, k), u(r + 1), acc);
+        if (j < ny - 1) acc = fmaT((T)coef(PBCG_N, i, j, k), u(r + nx), acc);
+        if (k < nz - 1) acc = fmaT((T)coef(PBCG_T, i, j, k), u(r + nxy), acc);
         return acc;
     }
 };
+using StencilOp = StencilOpT<double>;
 
 }  // namespace pbcg

@@ -53,6 +53,7 @@ struct pbicgstab_s {
     int prec;               // pbcg_prec of the handle
     int occ_pipe_prec, occ_plain_prec;
     double *minv, *rh, *sh, *zh, *qh, *wh;   // Jacobi: M^{-1} and the hat vectors
+    long long st_len[7][2];  // stencil: table elements the grid reaches (0: no table)
 };
 
 extern "C" {
@@ -353,6 +354,8 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
             q.n2 = c.data2 ? 1 : 0;
             q.value = c.value;
             o.c[d] = q;
+            h->st_len[d][0] = c.data ? max_index(c.stride, nx, ny, nz) + 1 : 0;
+            h->st_len[d][1] = c.data2 ? max_index(c.stride2, nx, ny, nz) + 1 : 0;
         }
         st = occupancy<pbcg::StencilOp>(&h->occ_pipe, &h->occ_plain);
         if (st == PBCG_OK) st = occupancy_prec<pbcg::StencilOp>(&h->occ_pipe_prec, &h->occ_plain_prec);
@@ -428,17 +431,18 @@ void pbicgstab_destroy(pbicgstab_t h) {
 // ---------------------------------------------------------------------------
 namespace {
 
-template <class Op32>
-pbcg_status launch_mixed(pbicgstab_s *h, const Op32 &a32, const pbcg::MixedArgs &m, int req_grid, int *grid_out) {
+template <class Op64, class Op32>
+pbcg_status launch_mixed(pbicgstab_s *h, const Op64 &a64, const Op32 &a32, const pbcg::MixedArgs &m, int req_grid,
+                         int *grid_out) {
     int occ = 0;
-    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::mixed_kernel<pbcg::CsrOp, Op32>, pbcg::kTPB, 0));
+    PBCG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbcg::mixed_kernel<Op64, Op32>, pbcg::kTPB, 0));
     if (occ < 1) return fail(PBCG_ERR_CUDA, "mixed-precision kernel cannot be resident on an SM");
     const int grid = pick_grid(h, occ, req_grid);
     *grid_out = grid;
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
     if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
-    void *params[3] = {(void *)&h->csr, (void *)&a32, (void *)&m};
-    PBCG_CUDA(cudaLaunchCooperativeKernel((const void *)pbcg::mixed_kernel<pbcg::CsrOp, Op32>, dim3(grid),
+    void *params[3] = {(void *)&a64, (void *)&a32, (void *)&m};
+    PBCG_CUDA(cudaLaunchCooperativeKernel((const void *)pbcg::mixed_kernel<Op64, Op32>, dim3(grid),
                                           dim3(pbcg::kTPB), params, 0, h->stream));
     if (h->ev1) PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
     return PBCG_OK;
@@ -452,11 +456,12 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
                                              pbcg_mixed_info *info) {
     if (info) memset(info, 0, sizeof(*info));
     if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
-    if (h->kind != 0) return fail(PBCG_ERR_ARG, "mixed precision needs a CSR handle");
     if (lowp_type != PBCG_VALUES_F32 && lowp_type != PBCG_VALUES_BF16)
         return fail(PBCG_ERR_ARG, "lowp_type must be PBCG_VALUES_F32 or PBCG_VALUES_BF16");
+    if (h->kind == 1 && (lowp_type != PBCG_VALUES_F32 || d_val_lowp))
+        return fail(PBCG_ERR_ARG, "stencil handles take d_val_lowp = NULL and PBCG_VALUES_F32");
     if (h->n > 0 && (!d_b || !d_x)) return fail(PBCG_ERR_ARG, "b or x is NULL");
-    if (h->n > 0 && !d_val_lowp) return fail(PBCG_ERR_ARG, "low-precision values are NULL");
+    if (h->kind == 0 && h->n > 0 && !d_val_lowp) return fail(PBCG_ERR_ARG, "low-precision values are NULL");
     if (!(rtol >= 0.0) || !(inner_rtol >= 0.0)) return fail(PBCG_ERR_ARG, "tolerances must be >= 0");
     if (max_outer < 0 || inner_maxit < 1) return fail(PBCG_ERR_ARG, "max_outer >= 0 and inner_maxit >= 1 required");
     pbcg_opts o{-1, 0, nullptr, 0, 0};
@@ -486,12 +491,57 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
     m.inner_maxit = inner_maxit;
     int grid = 0;
     pbcg_status st;
-    if (lowp_type == PBCG_VALUES_F32) {
+    if (h->kind == 1) {
+        // The coefficient tables rounded to FP32, in the part of the FP64
+        // vector area the 12 float vectors leave free (12 * s floats).
+        pbcg::StencilOpT<float> a32;
+        const pbcg::StencilOp &a64 = h->st;
+        a32.n = a64.n;
+        a32.nx = a64.nx;
+        a32.ny = a64.ny;
+        a32.nz = a64.nz;
+        a32.nxy = a64.nxy;
+        a32.dx = a64.dx;
+        a32.dy = a64.dy;
+        float *tab = f0 + 12 * s;
+        const size_t cap = 12 * s;
+        size_t used = 0;
+        for (int d = 0; d < 7; ++d) {
+            const pbcg::StCoef &q = a64.c[d];
+            pbcg::StCoefT<float> &q32 = a32.c[d];
+            q32.a1 = q.a1;
+            q32.b1 = q.b1;
+            q32.c1 = q.c1;
+            q32.a2 = q.a2;
+            q32.b2 = q.b2;
+            q32.c2 = q.c2;
+            q32.n2 = q.n2;
+            q32.value = (float)q.value;
+            const double *src[2] = {q.t1, q.t2};
+            const float **dst[2] = {&q32.t1, &q32.t2};
+            for (int t = 0; t < 2; ++t) {
+                *dst[t] = nullptr;
+                if (!src[t]) continue;
+                const size_t len = (size_t)h->st_len[d][t];
+                const size_t padded = (len + 31) / 32 * 32;
+                if (used + padded > cap)
+                    return fail(PBCG_ERR_ARG, "stencil coefficient tables too large for the mixed-precision "
+                                              "workspace (%zu floats free)", cap);
+                float *out = tab + used;
+                const int blocks = (int)((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096);
+                pbcg::to_float_kernel<<<blocks > 0 ? blocks : 1, 256, 0, h->stream>>>(src[t], out, (long long)len);
+                PBCG_CUDA(cudaGetLastError());
+                *dst[t] = out;
+                used += padded;
+            }
+        }
+        st = launch_mixed(h, a64, a32, m, o.grid, &grid);
+    } else if (lowp_type == PBCG_VALUES_F32) {
         const pbcg::CsrOpT<float> a32{h->n, h->csr.rowptr, h->csr.col, (const float *)d_val_lowp};
-        st = launch_mixed(h, a32, m, o.grid, &grid);
+        st = launch_mixed(h, h->csr, a32, m, o.grid, &grid);
     } else {
         const pbcg::CsrOpT<__nv_bfloat16> a16{h->n, h->csr.rowptr, h->csr.col, (const __nv_bfloat16 *)d_val_lowp};
-        st = launch_mixed(h, a16, m, o.grid, &grid);
+        st = launch_mixed(h, h->csr, a16, m, o.grid, &grid);
     }
     if (st != PBCG_OK) return st;
     pbcg::Control c;

@@ -1170,6 +1170,12 @@ __global__ void sync_timeout_probe_kernel(Control *ctl, double *slots, uint64_t 
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->status = ok ? (int)PBCG_OK : ld_relaxed_s32(&ctl->abort);
 }
 
+// out[k] = (float)in[k], k < len (FP32 copies of stencil coefficient tables).
+__global__ void to_float_kernel(const double *in, float *out, long long len) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < len; k += (long long)gridDim.x * blockDim.x)
+        out[k] = (float)in[k];
+}
+
 // y = A x, one row per thread, grid-stride.
 template <class Op>
 __global__ void __launch_bounds__(kTPB) spmv_kernel(const Op A, const double *x, double *y) {

@@ -448,15 +448,17 @@ class Solver:
 
     def solve_mixed(self, b, values_lowp, lowp_type=PBCG_VALUES_F32, x0=None, rtol=1e-10, max_outer=30,
                     inner_rtol=1e-4, inner_maxit=2000, history=False, **opts):
-        """FP64 refinement around FP32 Algorithm 9 (CSR handles); values_lowp is a
-        float32 or bfloat16 tensor with the CSR values. Returns (x, info[, history])."""
+        """FP64 refinement around FP32 Algorithm 9. CSR handles: values_lowp is a
+        float32 or bfloat16 tensor with the CSR values; stencil handles: None
+        (the library rounds the coefficient tables). Returns (x, info[, history])."""
         torch = self._torch()
         x = torch.zeros_like(b) if x0 is None else x0.clone()
         hist = None
         if history:
             hist = torch.full((max_outer + 1,), float("nan"), dtype=torch.float64, device=b.device)
             opts["d_history"] = hist.data_ptr()
-        st, info = pbicgstab_solve_mixed(self.h, values_lowp.data_ptr(), lowp_type, b.data_ptr(), x.data_ptr(),
+        vp = values_lowp.data_ptr() if values_lowp is not None else None
+        st, info = pbicgstab_solve_mixed(self.h, vp, lowp_type, b.data_ptr(), x.data_ptr(),
                                          rtol, max_outer, inner_rtol, inner_maxit, **opts)
         if st in (PBCG_ERR_ARG, PBCG_ERR_CUDA, PBCG_ERR_OOM, PBCG_ERR_TIMEOUT):
             raise PbcgError(st, pbicgstab_last_error())

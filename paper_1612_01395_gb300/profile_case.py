@@ -9,8 +9,9 @@ so a profiler can skip the warm-up launch and capture the next one:
 Problems: cd3d (3-D convection-diffusion, velocity (20 sin y, 20 cos z, 20 sin x),
 n^3 grid), cd2d (2-D, constant velocity (10, 10), n^2 grid).
 
---method mixed (CSR form only) runs one refinement step whose FP32 inner
-solve takes exactly --iters iterations (FP32 values; --bf16 for BF16 values).
+--method mixed runs one refinement step whose FP32 inner solve takes exactly
+--iters iterations (CSR form: FP32 values, --bf16 for BF16 values; stencil
+form: the coefficient tables rounded to FP32).
 """
 import argparse
 import json
@@ -42,10 +43,11 @@ def main(argv=None):
     xs = torch.from_numpy(P.splitmix64_uniform(0, st.n)).cuda()
     b = s.spmv(xs)
     if args.method == "mixed":
-        if args.form != "csr":
-            raise SystemExit("--method mixed needs --form csr")
-        A = P.stencil_to_csr(st)
-        lowp = torch.as_tensor(A.val).cuda().to(torch.bfloat16 if args.bf16 else torch.float32)
+        if args.form == "csr":
+            A = P.stencil_to_csr(st)
+            lowp = torch.as_tensor(A.val).cuda().to(torch.bfloat16 if args.bf16 else torch.float32)
+        else:
+            lowp = None
         typ = native.PBCG_VALUES_BF16 if args.bf16 else native.PBCG_VALUES_F32
         mk = dict(rtol=0.0, max_outer=1, inner_rtol=0.0, inner_maxit=args.iters, grid=args.grid)
         s.solve_mixed(b, lowp, typ, **mk)   # warm-up launch

@@ -73,12 +73,37 @@ def test_mixed_bf16_values_converge_on_well_conditioned_system():
     s.close()
 
 
-def test_mixed_rejects_stencil_handles_and_bad_arguments():
+@pytest.mark.parametrize("name", ["cd2d_64", "cd3d_20"])
+def test_mixed_fp32_stencil_form_reaches_1e10_true_residual(name):
+    """Stencil handles: the inner solves use the coefficient tables rounded to
+    FP32 (a summed coefficient is then added in FP32, so the inner operator can
+    differ from the rounded CSR values in the last bit); the FP64 refinement
+    still reaches the FP64 solution."""
+    st = P.cd2d_constant(64, (10.0, 10.0)) if name == "cd2d_64" else P.cd3d_trig(20)
+    A = P.stencil_to_csr(st)
+    b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
+    s = native.Solver.from_stencil(st)
+    x, info = s.solve_mixed(dev(b), None, native.PBCG_VALUES_F32, rtol=1e-10, max_outer=30, inner_rtol=1e-3,
+                            inner_maxit=2000)
+    assert info["status"] == native.PBCG_OK, info
+    xg = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - oracle.spmv(A, xg)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10
+    ref = oracle.pbicgstab(A, b, rtol=1e-12, maxit=3000, replace_period=20)
+    assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+    mo = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-3, inner_maxit=2000)
+    assert abs(info["outer"] - mo["outer"]) <= 2
+    s.close()
+
+
+def test_mixed_rejects_bad_arguments():
     import torch
     s = native.Solver.from_stencil(P.cd2d_constant(16))
     b = torch.ones(256, dtype=torch.float64, device="cuda")
-    with pytest.raises(native.PbcgError):
+    with pytest.raises(native.PbcgError):   # stencil handles take no values
         s.solve_mixed(b, torch.ones(10, dtype=torch.float32, device="cuda"))
+    with pytest.raises(native.PbcgError):   # nor BF16
+        s.solve_mixed(b, None, native.PBCG_VALUES_BF16)
     A = P.stencil_to_csr(P.cd2d_constant(16))
     c = native.Solver.from_csr(A)
     st, info = native.pbicgstab_solve_mixed(c.h, dev(A.val).to(torch.float32).data_ptr(), 7, b.data_ptr(),

@@ -48,8 +48,8 @@ ORACLE_ITERS = {"pbicgstab_rr50": 415, "bicgstab": 352}
 # the kernel sources it was taken on: SHA-256 over KERNEL_SOURCES.
 KERNEL_SOURCES = ["paper_1612_01395_gb300/csrc/device_common.cuh", "paper_1612_01395_gb300/csrc/operators.cuh",
                   "paper_1612_01395_gb300/csrc/solvers.cuh"]
-TRAFFIC_CAPTURE = {"bytes_per_launch": 984085750016 + 539634942720, "n": 16777216, "iters": 402, "grid": 1216,
-                   "sources_sha256": "bbe003a3535f829374b76b350c994a7f078832a657045a4a53318e3a8687a8dc"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 984047012864 + 539635155456, "n": 16777216, "iters": 402, "grid": 1216,
+                   "sources_sha256": "89eafea14f84123e0480fbc679ea4f1e166a3ba662c6ad87c8f0eb01da874e76"}
 
 
 def kernel_sources_sha256():
@@ -275,6 +275,49 @@ def timed_solves(solver, bd, x, steps, method, rr, barrier):
     torch.cuda.synchronize()
     barrier()
     return e0.elapsed_time(e1) / 1e3, infos
+
+
+def size_sweep(sizes=(16, 32, 48, 64, 96, 128, 192, 256), iters=100):
+    """Time per iteration of p-BiCGStab and BiCGStab on the n^3 convection-
+    diffusion stencil, 100 fixed iterations each (the same work for both
+    methods whatever their convergence): where the method pays on one GPU.
+    Small n is bound by the grid-wide synchronisations (2 per iteration
+    against 3 or 5), large n by FP64 arithmetic (Algorithm 9 does 1.3x the
+    FP64 work of Algorithm 7 per iteration)."""
+    import torch
+    from paper_1612_01395_gb300 import native, problems as P
+    out = {}
+    for n in sizes:
+        st = P.cd3d_trig(n)
+        s = native.Solver.from_stencil(st)
+        b = s.spmv(torch.from_numpy(P.splitmix64_uniform(SEED, st.n)).cuda())
+        row = {}
+        for method in ("pipelined", "standard"):
+            kw = dict(rtol=0.0, maxit=iters, fixed_iters=iters, method=method)
+            s.solve(b, **kw)
+            infos = [s.solve(b, **kw)[1] for _ in range(3)]
+            us = statistics.median(1e3 * i["kernel_ms"] / max(i["iters"], 1) for i in infos)
+            row["pbicgstab_us_per_iter" if method == "pipelined" else "bicgstab_us_per_iter"] = us
+        row["p_over_plain_time_per_iter"] = row["pbicgstab_us_per_iter"] / row["bicgstab_us_per_iter"]
+        out[str(st.n)] = row
+        s.close()
+    return out
+
+
+def jacobi_case(st, bd, x, barrier):
+    """Right Jacobi preconditioning (Algorithms 11 and 10, M = diag(A)) on the
+    same system and tolerance, one timed solve each after a warm-up."""
+    from paper_1612_01395_gb300 import native
+    s = native.Solver.from_stencil(st, prec=native.PBCG_PREC_JACOBI)
+    out = {}
+    for method, rr in (("pipelined", REPLACE_PERIOD), ("standard", 0)):
+        timed_solves(s, bd, x, 1, method, rr, barrier)
+        el, inf = timed_solves(s, bd, x, 1, method, rr, barrier)
+        r = summarize(el, inf, 1)
+        out["pbicgstab_jacobi" if method == "pipelined" else "bicgstab_jacobi"] = {
+            k: r[k] for k in ("value", "iters", "ms_per_iter", "rel_res_true", "grid")}
+    s.close()
+    return out
 
 
 def grid_sensitivity(solver, bd, x, grid):
@@ -590,6 +633,8 @@ def run_ours(args):
         out["csr"] = cmp_csr
         csolver.close()
         out["grid_sensitivity"] = grid_sensitivity(solver, bd, x, main["grid"])
+        out["jacobi"] = jacobi_case(st, bd, x, barrier)
+        out["size_sweep"] = size_sweep()
 
     if not args.no_mixed:
         out["mixed_precision"] = mixed_precision_case(args.mixed_n, args.steps, barrier)

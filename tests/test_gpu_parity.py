@@ -103,6 +103,24 @@ def test_stencil_and_csr_products_identical(name):
     np.testing.assert_array_equal(host(s1.spmv(x)), host(s2.spmv(x)))
 
 
+@pytest.mark.parametrize("method", ["pipelined", "standard"])
+def test_stencil_and_csr_solves_identical(method):
+    """The stencil and its sorted CSR assembly give bitwise identical rows, so
+    on the same grid (same summation order of the dot products) whole solves
+    -- iterates, counts, residual histories -- are bitwise identical too."""
+    st, A = problem("cd3d_20")
+    s1, s2 = native.Solver.from_stencil(st), native.Solver.from_csr(A)
+    b = dev(oracle.spmv(A, P.splitmix64_uniform(0, A.n)))
+    kw = dict(rtol=1e-12, maxit=2000, replace_period=20, method=method, grid=24, history=True)
+    x1, i1, h1 = s1.solve(b, **kw)
+    x2, i2, h2 = s2.solve(b, **kw)
+    assert i1["iters"] == i2["iters"] and i1["status"] == i2["status"] == native.PBCG_OK
+    np.testing.assert_array_equal(host(x1), host(x2))
+    np.testing.assert_array_equal(host(h1), host(h2))
+    s1.close()
+    s2.close()
+
+
 def oracle_run(method, A, b, **kw):
     fn = {"pipelined": oracle.pbicgstab, "standard": oracle.bicgstab}[method]
     return fn(A, b, **kw)

@@ -19,14 +19,17 @@ constexpr uint64_t kSyncTimeoutNs = 4000000000ull;   // 4 s per grid-wide wait
 struct Control {
     unsigned int arrivals;   // grid-sync arrivals, monotonic within one launch
     int abort;               // nonzero: pbcg_status that stopped the launch
-    int pad0[14];
+    unsigned int ready;      // large grids: 1 + the last exchange whose totals are published
+    int pad0[13];
     // result, written by block 0 at the end of a solve
     int iters, status, half_step, n_repl, grid_syncs, spmvs, inner_iters, pad1;
     double nr0, rel_rec, rel_true, pad2;
 };
 static_assert(sizeof(Control) <= 256, "control block must fit 256 bytes");
 constexpr size_t kControlBytes = 256;
-constexpr size_t kPartialBytes = 3ull * kMaxGrid * 8 * sizeof(double);   // 3 rotating slot buffers of 8 doubles
+// 3 rotating buffers of one 8-double slot per block, then 3 rotating 8-double
+// totals; rounded up to 256 bytes so the vectors after it stay 256-byte aligned
+constexpr size_t kPartialBytes = ((3ull * kMaxGrid + 3) * 8 * sizeof(double) + 255) / 256 * 256;
 
 // n / d for 0 <= n < 2^31 and 1 <= d < 2^31 by one multiply-high: the
 // round-up method of Granlund & Montgomery, "Division by invariant integers
@@ -131,21 +134,31 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double (*sm)[32]) {
 
 // Grid-wide exchange of a cooperative launch. Each block owns one 64-byte
 // slot (8 doubles) in each of 3 rotating buffers; exchange number e uses
-// buffer e % 3. Thread 0 of a block stores its K partial sums in its slot,
+// buffer e % 3. Thread 0 of a block stores its K block sums in its slot,
 // fences (gpu scope: every store of the phase, made visible to thread 0 by
-// __syncthreads, is ordered before the arrival), adds 1 to the arrival
-// counter, and spins on the counter until all blocks of exchange e arrived;
-// then every thread reads the slots. One poller per block on one word: polling
-// all slots from every thread congests the L2 and was measured slower. The
-// rotation keeps a slot from being rewritten while a slow block may still read
-// it (a block writes exchange e+3 only after all blocks arrived at e+2, i.e.
-// after all finished reading exchange e). Every wait is bounded (limit_ns,
+// __syncthreads, is ordered before the arrival) and adds 1 to the arrival
+// counter. Then, by grid size:
+//  * small grids: thread 0 spins on the counter until all blocks of exchange
+//    e arrived, and every block adds all slots in the same fixed order;
+//  * large grids (at least kLastReduceGrid blocks): the block whose arrival
+//    completes the count adds all slots (same fixed order), publishes the K
+//    totals and raises `ready`; the others spin on `ready` and read the
+//    totals. Every block adding every slot costs each SM (blocks per SM x
+//    blocks x K) FP64 additions per exchange -- about 12 us of its FP64 pipe
+//    at 1216 blocks -- against one extra flag hop.
+// One poller per block on one word: polling all slots from every thread
+// congests the L2 and was measured slower. The rotation keeps a slot or a
+// total from being rewritten while a slow block may still read it (exchange
+// e+3 is written only after all blocks arrived at e+2, i.e. after all finished
+// reading exchange e). Results are bitwise identical in every block and do
+// not depend on arrival order. Every wait is bounded (limit_ns,
 // kSyncTimeoutNs by default) and watches the abort flag.
 constexpr int kSlotDoubles = 8;
+constexpr int kLastReduceGrid = 512;
 
 struct GridSync {
     Control *ctl;
-    double *slots;      // [3][gridDim.x][kSlotDoubles]
+    double *slots;      // [3][gridDim.x][kSlotDoubles], then [3][kSlotDoubles] totals
     unsigned epoch;     // exchanges done by this block
     int count;          // exchanges performed (for diagnostics)
     uint64_t limit_ns = kSyncTimeoutNs;   // bound on each wait
@@ -154,65 +167,107 @@ struct GridSync {
 __device__ __forceinline__ double *slot_ptr(const GridSync &g, unsigned buf, int block) {
     return g.slots + ((size_t)buf * gridDim.x + block) * kSlotDoubles;
 }
+__device__ __forceinline__ double *totals_ptr(const GridSync &g, unsigned buf) {
+    return g.slots + ((size_t)3 * gridDim.x + buf) * kSlotDoubles;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-// Publish the K values of this block (thread 0 only) and wait for all blocks;
-// acc receives, per thread, the fixed-order sum of slots tid, tid+kTPB, ...
-template <int K>
-__device__ __forceinline__ bool exchange(GridSync &g, const double (&mine)[K], double (&acc)[K], int *sflag) {
-    const unsigned buf = g.epoch % 3u;
+// Thread 0: spin until *word >= target, bounded; false on abort or timeout.
+__device__ __forceinline__ bool wait_at_least(GridSync &g, const unsigned *word, unsigned target) {
+    const uint64_t t0 = globaltimer_ns();
+    while (ld_acquire_u32(word) < target) {
+        if (ld_relaxed_s32(&g.ctl->abort) != 0) return false;
+        if (globaltimer_ns() - t0 > g.limit_ns) {
+            atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// *sflag (shared, set to 1 once at kernel start) only ever goes from 1 to 0:
+// thread 0 clears it when a wait is abandoned, and every thread returns its
+// value after the barrier that follows. Never resetting it keeps a slow thread
+// from reading a later exchange's value.
+
+// Barrier without data.
+__device__ __forceinline__ bool grid_sync(GridSync &g, double (*)[32], int *sflag) {
+    __syncthreads();   // every thread's stores of this phase precede thread 0's fence
     if (threadIdx.x == 0) {
-        double *out = slot_ptr(g, buf, blockIdx.x);
-#pragma unroll
-        for (int k = 0; k < K; ++k) out[k] = mine[k];
         __threadfence();
         atomicAdd(&g.ctl->arrivals, 1u);
-        const unsigned target = (g.epoch + 1u) * gridDim.x;
-        const uint64_t t0 = globaltimer_ns();
-        while (ld_acquire_u32(&g.ctl->arrivals) < target) {
-            if (ld_relaxed_s32(&g.ctl->abort) != 0) { *sflag = 0; break; }
-            if (globaltimer_ns() - t0 > g.limit_ns) {
-                atomicCAS(&g.ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
-                *sflag = 0;
-                break;
-            }
-        }
+        if (!wait_at_least(g, &g.ctl->arrivals, (g.epoch + 1u) * gridDim.x)) *sflag = 0;
         __threadfence();
     }
     __syncthreads();
+    g.epoch++;
+    g.count++;
+    return *sflag != 0;
+}
+
+// Fixed-order sum over all slots of buffer buf, returned in every thread.
+template <int K>
+__device__ __forceinline__ void sum_slots(const GridSync &g, unsigned buf, double (&v)[K], double (*sm)[32]) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (int k = 0; k < K; ++k) v[k] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += kTPB) {
         const double *src = slot_ptr(g, buf, b);
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __ldcg(src + k);
+        for (int k = 0; k < K; ++k) v[k] += __ldcg(src + k);
     }
-    const bool all_ok = *sflag != 0;
-    g.epoch++;
-    g.count++;
-    return all_ok;
-}
-
-// Barrier without data (a dummy value is exchanged).
-__device__ __forceinline__ bool grid_sync(GridSync &g, double (*sm)[32], int *sflag) {
-    if (threadIdx.x == 0) *sflag = 1;
-    __syncthreads();   // every thread's stores of this phase precede thread 0's fence
-    const double one[1] = {1.0};
-    double acc[1];
-    return exchange<1>(g, one, acc, sflag);
+    block_sum<K>(v, sm);
 }
 
 // Barrier that also returns, in every thread of every block, the same
 // fixed-order sum over the grid of the K per-thread values v.
 template <int K>
 __device__ __forceinline__ bool grid_sum(GridSync &g, double (&v)[K], double (*sm)[32], int *sflag) {
-    if (threadIdx.x == 0) *sflag = 1;
+    static_assert(K <= kSlotDoubles, "at most 8 values per exchange");
+    __shared__ int last;
     block_sum<K>(v, sm);   // ends with __syncthreads
-    double acc[K];
-    if (!exchange<K>(g, v, acc, sflag)) return false;
-    block_sum<K>(acc, sm);
+    const unsigned buf = g.epoch % 3u;
+    const unsigned target = (g.epoch + 1u) * gridDim.x;
+    const bool by_last = gridDim.x >= (unsigned)kLastReduceGrid;
+    if (threadIdx.x == 0) {
+        double *out = slot_ptr(g, buf, blockIdx.x);
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = acc[k];
-    return true;
+        for (int k = 0; k < K; ++k) out[k] = v[k];
+        __threadfence();
+        const unsigned before = atomicAdd(&g.ctl->arrivals, 1u);
+        last = before == target - 1u;
+        if (!by_last) {
+            if (!wait_at_least(g, &g.ctl->arrivals, target)) *sflag = 0;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (!by_last) {
+        sum_slots<K>(g, buf, v, sm);
+    } else if (last) {
+        sum_slots<K>(g, buf, v, sm);   // every slot is visible: all blocks fenced before arriving
+        if (threadIdx.x == 0) {
+            double *tot = totals_ptr(g, buf);
+#pragma unroll
+            for (int k = 0; k < K; ++k) tot[k] = v[k];
+            __threadfence();
+            st_release_u32(&g.ctl->ready, g.epoch + 1u);
+        }
+    } else {
+        if (threadIdx.x == 0) {
+            if (!wait_at_least(g, &g.ctl->ready, g.epoch + 1u)) *sflag = 0;
+            __threadfence();
+        }
+        __syncthreads();
+        const double *tot = totals_ptr(g, buf);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = __ldcg(tot + k);
+    }
+    g.epoch++;
+    g.count++;
+    __syncthreads();   // `last` is rewritten by the next exchange
+    return *sflag != 0;
 }
 
 // Synchronisation policy of a solve owned by one thread block (batched

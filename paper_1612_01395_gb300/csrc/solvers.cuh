@@ -611,6 +611,7 @@ template <class Op, bool Prec>
 __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
+    if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier
     GridSync g{a.ctl, a.partials, 0u, 0};   // partials: the exchange slots
     const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
@@ -878,6 +879,7 @@ template <class Op, bool Prec>
 __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
+    if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier
     GridSync g{a.ctl, a.partials, 0u, 0};   // partials: the exchange slots
     const int lo = (int)((long long)blockIdx.x * a.n / gridDim.x);
     const int hi = (int)((long long)(blockIdx.x + 1) * a.n / gridDim.x);
@@ -921,6 +923,7 @@ template <class Op64, class Op32>
 __global__ void __launch_bounds__(kTPB, 8) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
+    if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier
     GridSync g{m.ctl, m.partials, 0u, 0};
     const int lo = (int)((long long)blockIdx.x * m.n / gridDim.x);
     const int hi = (int)((long long)(blockIdx.x + 1) * m.n / gridDim.x);
@@ -1165,6 +1168,7 @@ __global__ void sync_timeout_probe_kernel(Control *ctl, double *slots, uint64_t 
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
     if (blockIdx.x == gridDim.x - 1) return;
+    if (threadIdx.x == 0) sflag = 1;
     GridSync g{ctl, slots, 0u, 0, limit_ns};
     const bool ok = grid_sync(g, sm, &sflag);
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->status = ok ? (int)PBCG_OK : ld_relaxed_s32(&ctl->abort);

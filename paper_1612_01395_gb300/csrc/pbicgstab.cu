@@ -54,6 +54,7 @@ struct pbicgstab_s {
     int occ_pipe_prec, occ_plain_prec;
     double *minv, *rh, *sh, *zh, *qh, *wh;   // Jacobi: M^{-1} and the hat vectors
     long long st_len[7][2];  // stencil: table elements the grid reaches (0: no table)
+    long long nnz;           // stored entries (stencil: 7 per row), for the launch shape
 };
 
 extern "C" {
@@ -153,10 +154,27 @@ int pick_grid(const pbicgstab_s *h, int occ, int req) {
     int max_grid = occ * h->num_sms;
     if (max_grid > pbcg::kMaxGrid) max_grid = pbcg::kMaxGrid;
     if (req > 0) return req < max_grid ? req : max_grid;
-    // one row per thread while that leaves blocks to spare (small n: fewer
-    // blocks make each grid-wide exchange cheaper and the FP64 work per warp
-    // is the same); all co-resident blocks for large n
-    long long want = ((long long)h->n + pbcg::kTPB - 1) / pbcg::kTPB;
+    // The time of an iteration is the sweep (rows per thread, one after the
+    // other) plus the grid-wide exchanges, whose cost grows with the number of
+    // blocks. Block counts by work, measured on GB300 for both methods (60
+    // iterations; the optimum was flat within a few per cent around these).
+    // Work w = rows x max(1, entries per row / 7): for 5- and 7-point stencils
+    // 128 blocks up to w = 80k, then 2, 3, 4, 5 blocks per SM up to 180k,
+    // 400k, 1.2M, 3M and all co-resident blocks beyond; never fewer than one
+    // row per thread up to that count. Rows of ~21 random entries preferred
+    // one row per thread up to 256 blocks, which the work scaling gives.
+    const long long n = h->n;
+    const double per_row = n > 0 ? (double)h->nnz / (double)n : 0.0;
+    const double w = (double)n * (per_row > 7.0 ? per_row / 7.0 : 1.0);
+    long long want;
+    if (w <= 80000.0) {
+        want = 128;
+    } else {
+        const int per_sm = w <= 180000.0 ? 2 : w <= 400000.0 ? 3 : w <= 1200000.0 ? 4 : w <= 3000000.0 ? 5 : occ;
+        want = (long long)per_sm * h->num_sms;
+    }
+    const long long one_row = (n + pbcg::kTPB - 1) / pbcg::kTPB;
+    if (want > one_row) want = one_row;
     if (want < 1) want = 1;
     return (int)(want < max_grid ? want : max_grid);
 }
@@ -290,6 +308,7 @@ pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr
     if (st == PBCG_OK) {
         h->kind = 0;
         h->csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        h->nnz = nnz;
         st = occupancy<pbcg::CsrOp>(&h->occ_pipe, &h->occ_plain);
         if (st == PBCG_OK) st = occupancy_prec<pbcg::CsrOp>(&h->occ_pipe_prec, &h->occ_plain_prec);
     }
@@ -332,6 +351,7 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
     pbcg_status st = common_init(h, (int32_t)nn, prec, d_workspace, ws_bytes, stream);
     if (st == PBCG_OK) {
         h->kind = 1;
+        h->nnz = 7 * nn;
         pbcg::StencilOp &o = h->st;
         o.n = (int)nn;
         o.nx = nx;
@@ -799,6 +819,7 @@ extern "C" pbcg_status pbicgstab_solve_csr_noalloc(int32_t n, int32_t nnz, const
     if (st == PBCG_OK) {
         h.kind = 0;
         h.csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        h.nnz = nnz;
         st = occupancy<pbcg::CsrOp>(&h.occ_pipe, &h.occ_plain);
     }
     if (st == PBCG_OK) st = check_csr(&h, n, nnz, d_rowptr, d_col);

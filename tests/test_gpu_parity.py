@@ -224,10 +224,13 @@ def test_deterministic_and_grid_independent():
     x1, i1 = s.solve(bd, rtol=0.0, maxit=STEP_ITERS, fixed_iters=STEP_ITERS)
     x2, i2 = s.solve(bd, rtol=0.0, maxit=STEP_ITERS, fixed_iters=STEP_ITERS)
     np.testing.assert_array_equal(host(x1), host(x2))
-    for g in (1, 3, 64, 250):
+    # grids of 512 blocks and more reduce through the last block to arrive
+    for g in (1, 3, 64, 250, 600, 1216):
         xg, ig = s.solve(bd, rtol=0.0, maxit=STEP_ITERS, fixed_iters=STEP_ITERS, grid=g)
         assert ig["grid"] == g
         assert rel(host(xg), ref.x) <= X_TOL
+        xh, ih = s.solve(bd, rtol=0.0, maxit=STEP_ITERS, fixed_iters=STEP_ITERS, grid=g)
+        np.testing.assert_array_equal(host(xg), host(xh))
 
 
 def test_initial_guess_and_host_entry_point():

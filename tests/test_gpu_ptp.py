@@ -61,19 +61,30 @@ def test_ptp1_iterations_in_paper_range(method, rp):
 
 def test_ptp1_attainable_accuracy_matches_paper():
     """Figure 4: BiCGStab 5.8e-12, p-BiCGStab 1.7e-9, p-BiCGStab-rr 2.5e-12
-    within 2000 iterations (replacement every 100, at most 10). p-BiCGStab is
-    taken at its best of fixed runs of 400..650 iterations (its true residual
-    grows again later)."""
+    within 2000 iterations (replacement every 100, at most 10).
+
+    BiCGStab and p-BiCGStab-rr reach the attainable-accuracy floor, which is
+    stable. p-BiCGStab without replacement stalls where the rounding errors of
+    its recurrences have accumulated (Section 4.2), and where depends on the
+    summation order. On this GPU, its best true residual over fixed runs of
+    350..700 iterations is 7e-10 to 2e-8 over five block counts (the paper
+    reports one run on 240 processes). So its pin is the median over those
+    five summation orders, with the same factor 10, and it must stay two
+    orders above the other two methods."""
     g = golden()
     s, b = ptp(P.ptp1(1000))
     x, _ = s.solve(b, rtol=1e-17, maxit=2000, method="standard")
     std = true_norm(s, b, x)
     x, _ = s.solve(b, rtol=1e-17, maxit=2000, replace_period=100, max_replacements=10)
     rr = true_norm(s, b, x)
-    pipe = min(true_norm(s, b, s.solve(b, rtol=0.0, maxit=k, fixed_iters=k)[0]) for k in range(400, 651, 50))
+    levels = []
+    for grid in (304, 608, 760, 912, 1216):
+        levels.append(min(true_norm(s, b, s.solve(b, rtol=0.0, maxit=k, fixed_iters=k, grid=grid)[0])
+                          for k in range(350, 701, 25)))
+    pipe = float(np.median(levels))
     for got, key in ((std, "ptp1_attained_bicgstab"), (rr, "ptp1_attained_pbicgstab_rr"),
                      (pipe, "ptp1_attained_pbicgstab")):
-        assert g[key] / 10 <= got <= g[key] * 10, (key, got)
+        assert g[key] / 10 <= got <= g[key] * 10, (key, got, levels)
     assert pipe > 100 * max(std, rr)
     s.close()
 

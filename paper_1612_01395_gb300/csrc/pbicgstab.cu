@@ -6,11 +6,23 @@
 #include <mutex>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pbicgstab.h"
 #include "adjoint.cuh"
 #include "solvers.cuh"
 
 namespace {
+
+// A named range on the host timeline of profilers that read NVTX (header-only
+// NVTX3: without an attached tool each call is a no-op). A solve is one
+// kernel, so ranges mark library calls, not solver phases.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 thread_local char g_err[512] = "";
 
@@ -394,11 +406,13 @@ pbcg_status pbicgstab_create_stencil(const pbcg_stencil *desc, pbcg_prec prec, v
 
 pbcg_status pbicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
                             int32_t replace_period, const pbcg_opts *opts, pbcg_info *info) {
+    TraceRange tr("pbicgstab_solve");
     return run_solve(h, true, d_b, d_x, rtol, maxit, replace_period, opts, info);
 }
 
 pbcg_status bicgstab_solve(pbicgstab_t h, const double *d_b, double *d_x, double rtol, int32_t maxit,
                            const pbcg_opts *opts, pbcg_info *info) {
+    TraceRange tr("bicgstab_solve");
     return run_solve(h, false, d_b, d_x, rtol, maxit, 0, opts, info);
 }
 
@@ -474,6 +488,7 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
                                              const double *d_b, double *d_x, double rtol, int32_t max_outer,
                                              double inner_rtol, int32_t inner_maxit, const pbcg_opts *opts,
                                              pbcg_mixed_info *info) {
+    TraceRange tr("pbicgstab_solve_mixed");
     if (info) memset(info, 0, sizeof(*info));
     if (!h) return fail(PBCG_ERR_ARG, "handle is NULL");
     if (lowp_type != PBCG_VALUES_F32 && lowp_type != PBCG_VALUES_BF16)
@@ -622,6 +637,7 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
                                                double *d_x, double rtol, int32_t maxit, int32_t replace_period,
                                                const pbcg_batch_opts *opts, void *d_workspace, size_t ws_bytes,
                                                pbcg_batch_result *d_results, void *stream) {
+    TraceRange tr("pbicgstab_solve_batched");
     if (!batch) return fail(PBCG_ERR_ARG, "batch is NULL");
     if (batch->nsys < 0 || batch->nnz < 0 || total_rows < 0) return fail(PBCG_ERR_ARG, "negative size");
     if (batch->nsys == 0) return PBCG_OK;

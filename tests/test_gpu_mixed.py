@@ -96,6 +96,24 @@ def test_mixed_fp32_stencil_form_reaches_1e10_true_residual(name):
     s.close()
 
 
+def test_mixed_on_a_large_grid_is_deterministic_and_converges():
+    """1024 blocks on a small system: the reductions go through the last block
+    to arrive; two runs give the same bits and reach the FP64 solution."""
+    import torch
+    A = systems()["cd3d_20"]
+    b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
+    s = native.Solver.from_csr(A)
+    v32 = dev(A.val).to(torch.float32)
+    kw = dict(rtol=1e-10, max_outer=30, inner_rtol=1e-3, inner_maxit=2000, grid=1024)
+    x1, i1 = s.solve_mixed(dev(b), v32, native.PBCG_VALUES_F32, **kw)
+    x2, i2 = s.solve_mixed(dev(b), v32, native.PBCG_VALUES_F32, **kw)
+    assert i1["status"] == native.PBCG_OK and i1["grid"] == 1024
+    np.testing.assert_array_equal(x1.cpu().numpy(), x2.cpu().numpy())
+    true_rel = np.linalg.norm(b - oracle.spmv(A, x1.cpu().numpy())) / np.linalg.norm(b)
+    assert true_rel <= 1e-10
+    s.close()
+
+
 def test_mixed_rejects_bad_arguments():
     import torch
     s = native.Solver.from_stencil(P.cd2d_constant(16))

@@ -54,7 +54,10 @@ def make(name, form):
 @pytest.mark.parametrize("name", ["cd2d_64", "cd3d_20", "scaled_rand"])
 @pytest.mark.parametrize("form", ["csr", "stencil"])
 @pytest.mark.parametrize("method", ["pipelined", "standard"])
-def test_preconditioned_first_iterations_match_oracle(name, form, method):
+@pytest.mark.parametrize("grid", [0, 1024], ids=["default_grid", "grid1024"])
+def test_preconditioned_first_iterations_match_oracle(name, form, method, grid):
+    """grid 1024: the reductions go through the last block to arrive (512
+    blocks and more)."""
     s, A = make(name, form)
     minv = oracle.jacobi_minv(A)
     b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
@@ -63,7 +66,7 @@ def test_preconditioned_first_iterations_match_oracle(name, form, method):
     assert ref.status == oracle.CONVERGED
     k = min(20, ref.iters - (1 if ref.half_step else 0))
     fx = fn(A, minv, b, rtol=0.0, maxit=k, fixed_iters=k)
-    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=k, fixed_iters=k, history=True, method=method)
+    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=k, fixed_iters=k, history=True, method=method, grid=grid)
     assert info["status"] == native.PBCG_OK and info["iters"] == k
     xg = x.cpu().numpy()
     assert np.linalg.norm(xg - fx.x) / np.linalg.norm(fx.x) <= X_TOL

@@ -231,9 +231,10 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
     a.replace_period = pipelined ? replace_period : 0;
     a.max_repl = o.max_replacements;
     // Variant 3 saves two grid synchronisations per iteration at the price of
-    // 18 more FP64 operations per row; at ~1.9 FP64 FMA/clk/SM and ~1.4 us per
-    // synchronisation the two break even near n = 1e5.
-    a.variant = o.plain_variant ? o.plain_variant : (h->n < 100000 ? 3 : 5);
+    // 18 more FP64 operations per row. Measured per iteration on 3-D
+    // convection-diffusion: variant 3 is faster up to 110k unknowns (33.0 vs
+    // 34.1 us), variant 5 from 176k (42.5 vs 43.1 us; 65 vs 74 us at 512k).
+    a.variant = o.plain_variant ? o.plain_variant : (h->n < 150000 ? 3 : 5);
     a.minv = h->prec == PBCG_PREC_JACOBI ? h->minv : nullptr;
     a.rh = h->rh;
     a.sh = h->sh;

@@ -629,6 +629,8 @@ def run_ours(args):
             r = summarize(el, inf, ksteps)
             r["hbm_gbs_per_iter"] = bytes_per_iter(n, "csr") * r["iters"] / (r["kernel_ms"] / 1e3) / 1e9 \
                 if method == "pipelined" else None
+            if r["hbm_gbs_per_iter"] is not None:
+                r["hbm_frac_of_measured_peak"] = r["hbm_gbs_per_iter"] / hbm_peak
             cmp_csr["pbicgstab" if method == "pipelined" else "bicgstab"] = r
         out["csr"] = cmp_csr
         csolver.close()

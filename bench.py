@@ -277,6 +277,28 @@ def timed_solves(solver, bd, x, steps, method, rr, barrier):
     return e0.elapsed_time(e1) / 1e3, infos
 
 
+def small_2d_case(barrier, m=64, steps=20):
+    """The latency-bound workload: 2-D convection-diffusion on an m x m grid,
+    velocity (10, 10), CSR form, x* ~ U[-1,1], b = A x*, x0 = 0, both methods
+    to rtol 1e-8 (no replacement); mean time of `steps` solves after a warm-up."""
+    import torch
+    from paper_1612_01395_gb300 import native, problems as P
+    A = P.stencil_to_csr(P.cd2d_constant(m, (10.0, 10.0)))
+    s = native.Solver.from_csr(A)
+    b = s.spmv(torch.from_numpy(P.splitmix64_uniform(SEED, A.n)).cuda())
+    x = torch.zeros_like(b)
+    out = {"workload": f"2-D convection-diffusion {m}^2 (n={A.n}), velocity (10,10), CSR (nnz={A.nnz}), rtol {RTOL:g}"}
+    for method in ("pipelined", "standard"):
+        timed_solves(s, b, x, 3, method, 0, barrier)
+        el, inf = timed_solves(s, b, x, steps, method, 0, barrier)
+        r = summarize(el, inf, steps)
+        out["pbicgstab" if method == "pipelined" else "bicgstab"] = {
+            k: r[k] for k in ("value", "iters", "ms_per_iter", "rel_res_true", "grid", "grid_syncs")}
+    out["speedup_p_vs_bicgstab"] = out["bicgstab"]["value"] / out["pbicgstab"]["value"]
+    s.close()
+    return out
+
+
 def size_sweep(sizes=(16, 32, 48, 64, 96, 128, 192, 256), iters=100):
     """Time per iteration of p-BiCGStab and BiCGStab on the n^3 convection-
     diffusion stencil, 100 fixed iterations each (the same work for both
@@ -437,11 +459,13 @@ def batched_case(nsys, steps, barrier):
     bs = native.BatchSolver(B)
     b = torch.from_numpy(B.b).cuda()
     x = torch.zeros_like(b)
+    # the library's autotuner picks the launch shape (cluster size, threshold)
+    cs, cm, tune_ms = bs.autotune(b, x, rtol=RTOL, maxit=MAXIT)
     s = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         x.zero_()
-        bs.launch(b, x, rtol=RTOL, maxit=MAXIT, stream=s)
+        bs.launch(b, x, rtol=RTOL, maxit=MAXIT, stream=s, cluster_size=cs, cluster_min_rows=cm)
     g.replay()
     torch.cuda.synchronize()
     k = max(1, min(steps, 3))
@@ -471,6 +495,7 @@ def batched_case(nsys, steps, barrier):
     return {"workload": f"{B.nsys} random sparse systems, sizes log-uniform 1k-64k (total {B.total_rows} rows, "
                         f"{int(B.rowptr[-1])} nnz), rtol {RTOL:g}, one launch replayed from a CUDA graph",
             "value": sec, "unit": "s", "systems_converged": int(np.sum(res["status"] == native.PBCG_OK)),
+            "launch_shape": {"cluster_size": cs, "cluster_min_rows": cm, "autotuner_ms": tune_ms},
             "iters_total": int(res["iters"].sum()), "iters_max": int(res["iters"].max()),
             "max_rel_res_true": float(res["rel_res_true"].max()), "generation_s": gen_s,
             "single_system_solver_est_s": t_single / frac if frac > 0 else None,
@@ -637,6 +662,7 @@ def run_ours(args):
         out["grid_sensitivity"] = grid_sensitivity(solver, bd, x, main["grid"])
         out["jacobi"] = jacobi_case(st, bd, x, barrier)
         out["size_sweep"] = size_sweep()
+        out["small_2d"] = small_2d_case(barrier)
 
     if not args.no_mixed:
         out["mixed_precision"] = mixed_precision_case(args.mixed_n, args.steps, barrier)

@@ -284,6 +284,19 @@ pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t total_rows,
                                     double rtol, int32_t maxit, int32_t replace_period, const pbcg_batch_opts *opts,
                                     void *d_workspace, size_t ws_bytes, pbcg_batch_result *d_results, void *stream);
 
+/* Launch-shape autotuner for pbicgstab_solve_batched (no counterpart in the
+ * paper): solves the batch once per candidate shape (cluster size 1, 2, 4, 8
+ * or 16; cluster_min_rows 512, 4096 or 16384), each from x0 = 0 and timed
+ * with CUDA events on `stream`, after one warm-up solve; then solves once
+ * more with the fastest shape, so that on return d_x and d_results hold that
+ * solve. *best receives the shape and *best_ms (if not NULL) its time. Other
+ * arguments as pbicgstab_solve_batched; d_x is overwritten. Shapes the GPU
+ * cannot make resident are skipped. Blocks the calling thread. */
+pbcg_status pbicgstab_batched_autotune(const pbcg_batch *batch, int64_t total_rows, const double *d_b, double *d_x,
+                                       double rtol, int32_t maxit, int32_t replace_period, void *d_workspace,
+                                       size_t ws_bytes, pbcg_batch_result *d_results, void *stream,
+                                       pbcg_batch_opts *best, float *best_ms);
+
 /* Adjoint solves (an extension: reverse-mode gradients through a solve; the
  * paper has no counterpart). For x = A^{-1} b and a loss L(x), lambda solves
  * A^T lambda = dL/dx; then dL/db = lambda and dL/da_ij = -lambda_i x_j. */

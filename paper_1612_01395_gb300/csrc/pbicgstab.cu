@@ -716,6 +716,70 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     return PBCG_OK;
 }
 
+extern "C" pbcg_status pbicgstab_batched_autotune(const pbcg_batch *batch, int64_t total_rows, const double *d_b,
+                                                  double *d_x, double rtol, int32_t maxit, int32_t replace_period,
+                                                  void *d_workspace, size_t ws_bytes, pbcg_batch_result *d_results,
+                                                  void *stream, pbcg_batch_opts *best, float *best_ms) {
+    TraceRange tr("pbicgstab_batched_autotune");
+    if (!best) return fail(PBCG_ERR_ARG, "best is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    static const pbcg_batch_opts kCandidates[] = {
+        {1, 0, 1}, {2, 0, 512}, {4, 0, 512}, {8, 0, 512}, {16, 0, 512},
+        {4, 0, 4096}, {8, 0, 4096}, {16, 0, 4096}, {16, 0, 16384},
+    };
+    constexpr int kCount = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PBCG_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(PBCG_ERR_CUDA, "cudaEventCreate failed");
+    }
+    pbcg_status status = PBCG_OK;
+    float best_t = 0.0f;
+    int best_i = -1;
+    // a warm-up solve, then one timed solve per shape, each from x0 = 0
+    for (int c = -1; c < kCount && status == PBCG_OK; ++c) {
+        const pbcg_batch_opts &o = kCandidates[c < 0 ? 3 : c];
+        if (total_rows > 0 && cudaMemsetAsync(d_x, 0, (size_t)total_rows * sizeof(double), st) != cudaSuccess) {
+            status = fail(PBCG_ERR_CUDA, "cudaMemsetAsync failed");
+            break;
+        }
+        if (cudaEventRecord(e0, st) != cudaSuccess) { status = fail(PBCG_ERR_CUDA, "event record failed"); break; }
+        const pbcg_status r = pbicgstab_solve_batched(batch, total_rows, d_b, d_x, rtol, maxit, replace_period, &o,
+                                                      d_workspace, ws_bytes, d_results, stream);
+        if (r == PBCG_ERR_CUDA && c >= 0) continue;   // a cluster shape the GPU cannot make resident
+        if (r != PBCG_OK) { status = r; break; }
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            status = fail(PBCG_ERR_CUDA, "event synchronisation failed");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (c >= 0 && (best_i < 0 || ms < best_t)) {
+            best_t = ms;
+            best_i = c;
+        }
+    }
+    // the best shape runs last, so d_x and d_results hold its solves
+    if (status == PBCG_OK && best_i >= 0) {
+        if (total_rows > 0 && cudaMemsetAsync(d_x, 0, (size_t)total_rows * sizeof(double), st) != cudaSuccess)
+            status = fail(PBCG_ERR_CUDA, "cudaMemsetAsync failed");
+        if (status == PBCG_OK)
+            status = pbicgstab_solve_batched(batch, total_rows, d_b, d_x, rtol, maxit, replace_period,
+                                             &kCandidates[best_i], d_workspace, ws_bytes, d_results, stream);
+        if (status == PBCG_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            status = fail(PBCG_ERR_CUDA, "cudaStreamSynchronize failed");
+    } else if (status == PBCG_OK) {
+        status = fail(PBCG_ERR_CUDA, "no cluster shape could be launched");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != PBCG_OK) return status;
+    *best = kCandidates[best_i];
+    if (best_ms) *best_ms = best_t;
+    return PBCG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Adjoint building blocks: transpose and value gradient.
 // ---------------------------------------------------------------------------

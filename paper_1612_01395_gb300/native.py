@@ -33,7 +33,7 @@ EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_workspace_bytes_prec", "pbicg
            "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
            "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched",
            "pbicgstab_transpose_work_bytes", "pbicgstab_csr_transpose", "pbicgstab_csr_value_grad",
-           "pbicgstab_probe_sync_timeout"]
+           "pbicgstab_probe_sync_timeout", "pbicgstab_batched_autotune"]
 PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
@@ -149,6 +149,10 @@ def lib():
         L.pbicgstab_csr_transpose.restype = ctypes.c_int
         L.pbicgstab_csr_value_grad.argtypes = [i32, vp, vp, vp, vp, vp, vp]
         L.pbicgstab_probe_sync_timeout.argtypes = [vp, i32, ctypes.POINTER(i32)]
+        L.pbicgstab_batched_autotune.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32,
+                                                 vp, sz, vp, vp, ctypes.POINTER(PbcgBatchOpts),
+                                                 ctypes.POINTER(ctypes.c_float)]
+        L.pbicgstab_batched_autotune.restype = ctypes.c_int
         L.pbicgstab_probe_sync_timeout.restype = ctypes.c_int
         L.pbicgstab_csr_value_grad.restype = ctypes.c_int
         L.pbicgstab_solve_csr_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, f64, i32, i32,
@@ -301,6 +305,21 @@ class BatchSolver:
                                      opts, self.ws_ptr, self.ws_bytes, self.results.data_ptr(), st)
         if rc != PBCG_OK:
             raise PbcgError(rc, pbicgstab_last_error())
+
+    def autotune(self, b, x, rtol=1e-8, maxit=1000, replace_period=0, stream=None):
+        """Time the candidate launch shapes (library autotuner; x is overwritten
+        with the best shape's solution). Returns (cluster_size, cluster_min_rows, ms)."""
+        torch = self.torch
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        best = PbcgBatchOpts()
+        ms = ctypes.c_float(0.0)
+        rc = lib().pbicgstab_batched_autotune(ctypes.byref(self.desc), int(self.total), b.data_ptr(), x.data_ptr(),
+                                              float(rtol), int(maxit), int(replace_period), self.ws_ptr,
+                                              int(self.ws_bytes), self.results.data_ptr(), st, ctypes.byref(best),
+                                              ctypes.byref(ms))
+        if rc != PBCG_OK:
+            raise PbcgError(rc, pbicgstab_last_error())
+        return best.cluster_size, best.cluster_min_rows, ms.value
 
     def fetch_results(self):
         """Per-system results as a numpy structured array (synchronises)."""

@@ -119,3 +119,21 @@ def test_unsupported_cluster_size_is_rejected():
     x = torch.zeros_like(b)
     with pytest.raises(native.PbcgError):
         bs.launch(b, x, cluster_size=3)
+
+
+def test_autotuner_picks_a_launchable_shape_and_leaves_its_solution():
+    """The library autotuner times the candidate shapes; on return x holds the
+    solve of the chosen shape, bitwise equal to a direct launch with it."""
+    import torch
+    B = small_batch()
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    cs, cm, ms = bs.autotune(b, x, rtol=1e-8, maxit=1000)
+    assert cs in (1, 2, 4, 8, 16) and cm > 0 and ms > 0
+    assert np.all(bs.fetch_results()["status"] == native.PBCG_OK)
+    tuned = x.clone()
+    x.zero_()
+    bs.launch(b, x, rtol=1e-8, maxit=1000, cluster_size=cs, cluster_min_rows=cm)
+    torch.cuda.synchronize()
+    assert torch.equal(x, tuned)

@@ -137,3 +137,44 @@ def test_autotuner_picks_a_launchable_shape_and_leaves_its_solution():
     bs.launch(b, x, rtol=1e-8, maxit=1000, cluster_size=cs, cluster_min_rows=cm)
     torch.cuda.synchronize()
     assert torch.equal(x, tuned)
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_IDS)
+def test_degenerate_systems_in_a_batch(shape):
+    """An empty system, a 1x1 system and a 2x2 system among ordinary ones:
+    the empty one converges in 0 iterations, the others to the exact solution."""
+    import torch
+    base = P.random_batch(nsys=3, seed=5, nmin=200, nmax=900)
+    # systems: [base0, empty, 1x1 (a = 4), 2x2 diagonally dominant, base1, base2]
+    sys_csr = [base.system(0), None, P.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0])),
+               P.CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32),
+                     np.array([3.0, 1.0, -1.0, 2.0])), base.system(1), base.system(2)]
+    sizes, rowptr, col, val, bs_ = [], [0], [], [], []
+    for k, A in enumerate(sys_csr):
+        if A is None:
+            sizes.append(0)
+            continue
+        sizes.append(A.n)
+        off = rowptr[-1]
+        rowptr.extend((A.rowptr[1:].astype(np.int64) + off).tolist())
+        col.extend(A.col.tolist())
+        val.extend(A.val.tolist())
+        bs_.append(P.splitmix64_uniform(40 + k, A.n))
+    sizes = np.array(sizes, dtype=np.int64)
+    B = P.Batch(sizes=sizes, row_offset=np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64),
+                rowptr=np.array(rowptr, dtype=np.int32), col=np.array(col, dtype=np.int32),
+                val=np.array(val, dtype=np.float64), b=np.concatenate(bs_))
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    bs.launch(b, x, rtol=1e-12, maxit=500, replace_period=20, cluster_size=shape[0], cluster_min_rows=shape[1])
+    res = bs.fetch_results()
+    assert np.all(res["status"] == native.PBCG_OK), res
+    assert res["iters"][1] == 0
+    xg = x.cpu().numpy()
+    for k, A in enumerate(sys_csr):
+        if A is None:
+            continue
+        r0, r1 = int(B.row_offset[k]), int(B.row_offset[k + 1])
+        exact = np.linalg.solve(A.to_dense(), B.b[r0:r1])
+        assert np.linalg.norm(xg[r0:r1] - exact) <= 1e-9 * np.linalg.norm(exact), k

@@ -636,7 +636,8 @@ def run_ours(args):
            "config": dict(workload_config(n), parallelism="replicas only" if world > 1 else "single GPU"),
            "iters": main["iters"], "ms_per_iter": main["ms_per_iter"], "rel_res_true": main["rel_res_true"],
            "hbm_gbs_per_iter": gbs, "grid_syncs_per_solve": main["grid_syncs"], "grid": main["grid"],
-           "roofline": roofline, "clocks": clk, "gpu_launches": args.steps}
+           "roofline": roofline, "clocks": clk, "gpu_launches": args.steps,
+           "create_s": {"stencil": solver.create_s}}
 
     # comparison: standard BiCGStab on the same form, and both methods on CSR
     if not args.no_compare:
@@ -647,6 +648,7 @@ def run_ours(args):
         out["bicgstab"] = dict(plain, form="stencil")
         out["speedup_p_vs_bicgstab"] = plain["value"] / sec
         csolver = native.Solver.from_csr(A)
+        out["create_s"]["csr"] = csolver.create_s   # includes the device-side structure check
         cmp_csr = {}
         for method, rr in (("pipelined", REPLACE_PERIOD), ("standard", 0)):
             timed_solves(csolver, bd, x, 1, method, rr, barrier)

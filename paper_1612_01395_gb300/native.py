@@ -11,6 +11,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import time
 from typing import Optional
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -405,8 +406,12 @@ class Solver:
         val = torch.as_tensor(A.val, dtype=torch.float64).cuda()
         self._keep += [rowptr, col, val]
         ws, nb = self._workspace(A.n, stream, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         self.h = pbicgstab_create_csr(A.n, A.nnz, rowptr.data_ptr(), col.data_ptr() if A.nnz else None,
                                       val.data_ptr() if A.nnz else None, prec, ws, nb, self.stream.cuda_stream)
+        torch.cuda.synchronize()
+        self.create_s = time.perf_counter() - t0   # the C create call alone (arrays already on the device)
         return self
 
     @classmethod
@@ -431,7 +436,11 @@ class Solver:
                 cd.len2 = t2.numel()
                 cd.stride2[:] = [int(v) for v in c.stride2]
         ws, nb = self._workspace(st.n, stream, prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         self.h = pbicgstab_create_stencil(desc, prec, ws, nb, self.stream.cuda_stream)
+        torch.cuda.synchronize()
+        self.create_s = time.perf_counter() - t0   # the C create call alone (tables already on the device)
         return self
 
     def spmv(self, x):

@@ -7,7 +7,8 @@ so a profiler can skip the warm-up launch and capture the next one:
         --method pipelined --form stencil
 
 Problems: cd3d (3-D convection-diffusion, velocity (20 sin y, 20 cos z, 20 sin x),
-n^3 grid), cd2d (2-D, constant velocity (10, 10), n^2 grid).
+n^3 grid), cd2d (2-D, constant velocity (10, 10), n^2 grid), batch (--nsys
+random sparse systems of 1k-64k rows, one batched launch per repeat).
 
 --method mixed runs one refinement step whose FP32 inner solve takes exactly
 --iters iterations (CSR form: FP32 values, --bf16 for BF16 values; stencil
@@ -22,7 +23,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--problem", default="cd3d", choices=["cd3d", "cd2d"])
+    ap.add_argument("--problem", default="cd3d", choices=["cd3d", "cd2d", "batch"])
+    ap.add_argument("--nsys", type=int, default=64, help="systems of --problem batch")
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--iters", type=int, default=5, help="fixed iterations per solve (0: solve to --rtol)")
     ap.add_argument("--rtol", type=float, default=1e-8)
@@ -38,6 +40,27 @@ def main(argv=None):
     import torch
     from paper_1612_01395_gb300 import native, problems as P
     native.build()
+    if args.problem == "batch":
+        # random sparse systems, sizes log-uniform in 1k-64k, largest first; solved to --rtol
+        B = P.random_batch(nsys=args.nsys, seed=0)
+        bs = native.BatchSolver(B)
+        b = torch.from_numpy(B.b).cuda()
+        x = torch.zeros_like(b)
+        times = []
+        for rep in range(1 + args.repeat):   # the first launch is a warm-up
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bs.launch(b, x, rtol=args.rtol, maxit=1000)
+            e1.record()
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+        r = bs.fetch_results()
+        print(json.dumps({"problem": "batch", "nsys": B.nsys, "rows": B.total_rows, "ms": float(np.median(times)),
+                          "converged": int(np.sum(r["status"] == native.PBCG_OK)),
+                          "iters_total": int(r["iters"].sum())}))
+        return 0
     st = P.cd3d_trig(args.n) if args.problem == "cd3d" else P.cd2d_constant(args.n, (10.0, 10.0))
     s = native.Solver.from_stencil(st) if args.form == "stencil" else native.Solver.from_csr(P.stencil_to_csr(st))
     xs = torch.from_numpy(P.splitmix64_uniform(0, st.n)).cuda()

@@ -31,7 +31,6 @@ METRIC = "time-to-rel.res 1e-8 and HBM GB/s per iter, p-BiCGStab vs BiCGStab, 1 
 RTOL = 1e-8
 REPLACE_PERIOD = 50
 MAXIT = 20000
-INNER_MAXIT = 150          # iterations per inner solve of the mixed-precision refinement
 SEED = 0
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM
@@ -376,19 +375,26 @@ def summarize(elapsed, infos, steps):
 def mixed_precision_case(n, steps, barrier):
     """FP64 refinement around FP32 (and BF16-valued) Algorithm 9 against all-FP64
     p-BiCGStab, both to a true relative residual of 1e-10, on the n^3
-    convection-diffusion system in CSR form and in stencil form."""
+    convection-diffusion system in CSR form and in stencil form.
+
+    Inner solves stop at their tolerance or after a cap of iterations (a
+    restart): an FP32 Krylov solve can stagnate far above its tolerance, and
+    the next step's FP64 residual restarts it. The FP32 inner iteration counts
+    move by 15-25 % with the summation order (the grid), so each setting is
+    also solved at two more grid sizes and the median reported beside the
+    default-grid time."""
+    import statistics as stats
     import torch
     from paper_1612_01395_gb300 import native, problems as P
     st = P.cd3d_trig(n)
     A = P.stencil_to_csr(st)
     N = A.n
-    s = native.Solver.from_csr(A)
-    bd = s.spmv(torch.from_numpy(P.splitmix64_uniform(SEED, N)).cuda())
-    v32 = torch.as_tensor(A.val).cuda().to(torch.float32)
-    v16 = torch.as_tensor(A.val).cuda().to(torch.bfloat16)
+    solvers = {"csr": native.Solver.from_csr(A), "stencil": native.Solver.from_stencil(st)}
+    bd = solvers["stencil"].spmv(torch.from_numpy(P.splitmix64_uniform(SEED, N)).cuda())
+    vals = {"fp32": torch.as_tensor(A.val).cuda().to(torch.float32),
+            "bf16": torch.as_tensor(A.val).cuda().to(torch.bfloat16)}
     out = {"workload": f"3-D convection-diffusion {n}^3 (n={N}), CSR (nnz={A.nnz}) and stencil forms, "
                        f"true rel.res 1e-10"}
-    runs = {}
 
     def timed(fn, k):
         fn()
@@ -403,45 +409,44 @@ def mixed_precision_case(n, steps, barrier):
         return e0.elapsed_time(e1) / 1e3 / k, res
 
     k = max(1, min(steps, 3))
-    sec, (x64, i64) = timed(lambda: s.solve(bd, rtol=1e-10, maxit=MAXIT, replace_period=REPLACE_PERIOD), k)
-    runs["fp64_pbicgstab"] = {"value": sec, "iters": i64["iters"], "rel_res_true": i64["rel_res_true"],
-                              "status": native.STATUS_NAMES[i64["status"]]}
-    # inner solves are capped at INNER_MAXIT iterations (a restart): an FP32
-    # Krylov solve can stagnate far above its tolerance, and the FP64 residual
-    # of the next refinement step restarts it from the true residual
-    cases = [(f"mixed_fp32_inner{tau:g}", v32, native.PBCG_VALUES_F32, tau) for tau in (1e-1, 1e-2)]
-    cases.append(("mixed_bf16_inner0.01", v16, native.PBCG_VALUES_BF16, 1e-2))
-    for name, vals, typ, tau in cases:
+    x64 = {}
+    for form, s in solvers.items():
+        sec, (x, info) = timed(lambda: s.solve(bd, rtol=1e-10, maxit=MAXIT, replace_period=REPLACE_PERIOD), k)
+        x64[form] = x
+        out[f"{form}_fp64_pbicgstab"] = {"value": sec, "iters": info["iters"], "rel_res_true": info["rel_res_true"],
+                                         "status": native.STATUS_NAMES[info["status"]]}
+    cases = [("csr", "fp32", 1e-1, 50), ("csr", "fp32", 3e-2, 150), ("stencil", "fp32", 1e-1, 50),
+             ("stencil", "fp32", 3e-2, 150), ("csr", "bf16", 1e-2, 150)]
+    for form, vt, tau, cap in cases:
+        s = solvers[form]
+        v = None if form == "stencil" else vals[vt]
+        typ = native.PBCG_VALUES_BF16 if vt == "bf16" else native.PBCG_VALUES_F32
+        name = f"{form}_mixed_{vt}_inner{tau:g}_cap{cap}"
+
+        def run(grid=0):
+            return s.solve_mixed(bd, v, typ, rtol=1e-10, max_outer=60, inner_rtol=tau, inner_maxit=cap, grid=grid)
         try:
-            sec, (xm, im) = timed(lambda: s.solve_mixed(bd, vals, typ, rtol=1e-10, max_outer=40, inner_rtol=tau,
-                                                        inner_maxit=INNER_MAXIT), k)
+            sec, (xm, im) = timed(run, k)
         except native.PbcgError as e:
-            runs[name] = {"error": str(e)}
+            out[name] = {"error": str(e)}
             continue
-        err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
-        inner_bytes = (24 * 4 + 2 * (8 * A.nnz / N + 4)) * N   # FP32 vectors + FP32 CSR, per inner iteration
-        runs[name] = {"value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"], "inner_maxit": INNER_MAXIT,
-                      "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
-                      "rel_error_vs_fp64": err, "speedup_vs_fp64": runs["fp64_pbicgstab"]["value"] / sec,
-                      "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
-    s.close()
-    # stencil form: no matrix bytes; the inner solves use the coefficient tables rounded to FP32
-    ss = native.Solver.from_stencil(st)
-    sec, (x64s, i64s) = timed(lambda: ss.solve(bd, rtol=1e-10, maxit=MAXIT, replace_period=REPLACE_PERIOD), k)
-    runs["stencil_fp64_pbicgstab"] = {"value": sec, "iters": i64s["iters"], "rel_res_true": i64s["rel_res_true"],
-                                      "status": native.STATUS_NAMES[i64s["status"]]}
-    for tau in (1e-1, 1e-2):
-        sec, (xm, im) = timed(lambda: ss.solve_mixed(bd, None, native.PBCG_VALUES_F32, rtol=1e-10, max_outer=40,
-                                                     inner_rtol=tau, inner_maxit=INNER_MAXIT), k)
-        err = float(torch.linalg.norm(xm - x64s) / torch.linalg.norm(x64s))
-        inner_bytes = 24 * 4 * N   # FP32 vectors only, per inner iteration
-        runs[f"stencil_mixed_fp32_inner{tau:g}"] = {
-            "value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"], "inner_maxit": INNER_MAXIT,
-            "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
-            "rel_error_vs_fp64": err, "speedup_vs_fp64_stencil": runs["stencil_fp64_pbicgstab"]["value"] / sec,
-            "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
-    ss.close()
-    out.update(runs)
+        ref = out[f"{form}_fp64_pbicgstab"]["value"]
+        per_grid = {"default": sec}
+        if im["status"] == native.PBCG_OK:
+            for g in (1368, 1216):   # 9 and 8 blocks per SM, near the default 10: other summation orders
+                _, ig = run(g)
+                per_grid[str(g)] = ig["kernel_ms"] / 1e3
+        median = stats.median(per_grid.values())
+        err = float(torch.linalg.norm(xm - x64[form]) / torch.linalg.norm(x64[form]))
+        mat_bytes = 0 if form == "stencil" else 2 * ((4 if vt == "fp32" else 2) + 4) * A.nnz + 8 * (N + 1)
+        inner_bytes = 24 * 4 * N + mat_bytes   # FP32 vectors (+ low-precision CSR), per inner iteration
+        out[name] = {"value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"], "inner_maxit": cap,
+                     "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
+                     "rel_error_vs_fp64": err, "speedup_vs_fp64": ref / sec,
+                     "s_per_grid": per_grid, "median_s_over_grids": median, "median_speedup_vs_fp64": ref / median,
+                     "inner_gbs_est": inner_bytes * im["inner_iters"] / (im["kernel_ms"] / 1e3) / 1e9}
+    for s in solvers.values():
+        s.close()
     return out
 
 

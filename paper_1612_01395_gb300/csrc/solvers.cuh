@@ -166,6 +166,35 @@ __device__ __forceinline__ void dot_values(const DotAcc<T> (&acc)[K], double (&d
     for (int k = 0; k < K; ++k) d[k] = acc[k].value();
 }
 
+// G adjacent elements p[i..i+cnt) of a vector (cnt <= G; the rest read as 0)
+// and their store. G = 2 uses one 64-bit access when both are present: i is
+// even and the vectors are 8-byte aligned (the FP32 inner sweeps).
+template <int G, typename T>
+__device__ __forceinline__ void load_group(const T *p, int i, int cnt, T (&out)[G]) {
+    if constexpr (G == 2 && sizeof(T) == 4) {
+        if (cnt == 2) {
+            const float2 q = *reinterpret_cast<const float2 *>(p + i);
+            out[0] = q.x;
+            out[1] = q.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u) out[u] = u < cnt ? p[i + u] : T(0);
+}
+template <int G, typename T>
+__device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[G]) {
+    if constexpr (G == 2 && sizeof(T) == 4) {
+        if (cnt == 2) {
+            *reinterpret_cast<float2 *>(p + i) = make_float2(in[0], in[1]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+        if (u < cnt) p[i + u] = in[u];
+}
+
 // ===========================================================================
 // Algorithm 9 (pipelined BiCGStab) with the residual replacement of
 // Section 4.2 (r := b - A x, w := A r before the second reduction of iteration
@@ -181,14 +210,14 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     const VectorsT<T> &V = a.V;
     T *x = a.x;
     const bool fixed = a.fixed != 0;
-    // Rows per step of the two main sweeps. A step loads all its rows before
-    // storing any (the stores of one row may alias the loads of the next as
-    // far as the compiler knows). Rows are accumulated in the same order
-    // whatever the step. One row per step measured best for both types: FP64
-    // sweeps are bound by the FP64 pipe, and the latency-bound FP32 inner
-    // sweeps gain more from resident warps (the mixed kernel runs 10 blocks
-    // per SM) than from two rows per step at 8 blocks per SM.
-    constexpr int kRows = 1;
+    // Rows per thread and step of the two main sweeps: kGroup adjacent rows,
+    // loaded before any is stored (the stores of one row may alias the loads
+    // of the next as far as the compiler knows). FP64 sweeps are bound by the
+    // FP64 pipe and take one row. The FP32 inner sweeps are bound by load
+    // latency and take two adjacent rows with 64-bit vector accesses, which
+    // halves their load and store instructions; their callers give every
+    // block an even first row.
+    constexpr int kGroup = sizeof(T) == 4 ? 2 : 1;
 
     // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
     double d0[1];
@@ -238,45 +267,41 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         DotAcc<T> a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         const T al = (T)alpha, be = (T)beta, om = (T)omega;
         if (!replaced_rw) {
-            for (int i0 = lo + (int)threadIdx.x; i0 < hi; i0 += kRows * kTPB) {
-                T ti[kRows] = {}, ri[kRows] = {}, wi[kRows] = {}, si[kRows] = {}, zi[kRows] = {}, pi[kRows] = {},
-                  vi[kRows] = {}, r0i[kRows] = {};
+            for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
+                const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
+                T ti[kGroup] = {}, ri[kGroup], wi[kGroup], si[kGroup], zi[kGroup], pi[kGroup], vi[kGroup], r0i[kGroup];
 #pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const int i = i0 + u * kTPB;
-                    if (i < hi) {
-                        ti[u] = A.row(i, VecLoadT<T>{V.w});
-                        ri[u] = V.r[i];
-                        wi[u] = V.w[i];
-                        si[u] = V.s[i];
-                        zi[u] = V.z[i];
-                        pi[u] = V.p[i];
-                        vi[u] = V.v[i];
-                        r0i[u] = V.r0[i];
+                for (int u = 0; u < kGroup; ++u)
+                    if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
+                load_group(V.r, i0, cnt, ri);
+                load_group(V.w, i0, cnt, wi);
+                load_group(V.s, i0, cnt, si);
+                load_group(V.z, i0, cnt, zi);
+                load_group(V.p, i0, cnt, pi);
+                load_group(V.v, i0, cnt, vi);
+                load_group(V.r0, i0, cnt, r0i);
+                T pn[kGroup], sn[kGroup], zn[kGroup], qn[kGroup], yn[kGroup];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    pn[u] = fmaT(be, fmaT(-om, si[u], pi[u]), ri[u]);   // p_i
+                    sn[u] = fmaT(be, fmaT(-om, zi[u], si[u]), wi[u]);   // s_i, eq. (1)
+                    zn[u] = fmaT(be, fmaT(-om, vi[u], zi[u]), ti[u]);   // z_i, eq. (6)
+                    qn[u] = fmaT(-al, sn[u], ri[u]);                    // q_i
+                    yn[u] = fmaT(-al, zn[u], wi[u]);                    // y_i, eq. (4)
+                    if (u < cnt) {
+                        a1[0].add(qn[u], yn[u]);
+                        a1[1].add(yn[u], yn[u]);
+                        a1[2].add(qn[u], qn[u]);
+                        a1[3].add(r0i[u], sn[u]);
+                        a1[4].add(r0i[u], zn[u]);
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const int i = i0 + u * kTPB;
-                    if (i < hi) {
-                        const T pn = fmaT(be, fmaT(-om, si[u], pi[u]), ri[u]);   // p_i
-                        const T sn = fmaT(be, fmaT(-om, zi[u], si[u]), wi[u]);   // s_i, eq. (1)
-                        const T zn = fmaT(be, fmaT(-om, vi[u], zi[u]), ti[u]);   // z_i, eq. (6)
-                        const T qi = fmaT(-al, sn, ri[u]);                       // q_i
-                        const T yi = fmaT(-al, zn, wi[u]);                       // y_i, eq. (4)
-                        V.t[i] = ti[u];
-                        V.p[i] = pn;
-                        V.s[i] = sn;
-                        V.z[i] = zn;
-                        V.q[i] = qi;
-                        V.y[i] = yi;
-                        a1[0].add(qi, yi);
-                        a1[1].add(yi, yi);
-                        a1[2].add(qi, qi);
-                        a1[3].add(r0i[u], sn);
-                        a1[4].add(r0i[u], zn);
-                    }
-                }
+                store_group(V.t, i0, cnt, ti);
+                store_group(V.p, i0, cnt, pn);
+                store_group(V.s, i0, cnt, sn);
+                store_group(V.z, i0, cnt, zn);
+                store_group(V.q, i0, cnt, qn);
+                store_group(V.y, i0, cnt, yn);
             }
             ++spmvs;
         } else {
@@ -331,37 +356,34 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         DotAcc<T> a2[3];   // (r0,r) (r0,w) (r,r)
         const T om2 = (T)omega;
         if (!replace_now) {
-            for (int i0 = lo + (int)threadIdx.x; i0 < hi; i0 += kRows * kTPB) {
-                T vi[kRows] = {}, qi[kRows] = {}, yi[kRows] = {}, xi[kRows] = {}, pi[kRows] = {}, ti[kRows] = {},
-                  r0i[kRows] = {};
+            for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
+                const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
+                T vi[kGroup] = {}, qi[kGroup], yi[kGroup], xi[kGroup], pi[kGroup], ti[kGroup], r0i[kGroup];
 #pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const int i = i0 + u * kTPB;
-                    if (i < hi) {
-                        vi[u] = A.row(i, VecLoadT<T>{V.z});
-                        qi[u] = V.q[i];
-                        yi[u] = V.y[i];
-                        xi[u] = x[i];
-                        pi[u] = V.p[i];
-                        ti[u] = V.t[i];
-                        r0i[u] = V.r0[i];
+                for (int u = 0; u < kGroup; ++u)
+                    if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
+                load_group(V.q, i0, cnt, qi);
+                load_group(V.y, i0, cnt, yi);
+                load_group(x, i0, cnt, xi);
+                load_group(V.p, i0, cnt, pi);
+                load_group(V.t, i0, cnt, ti);
+                load_group(V.r0, i0, cnt, r0i);
+                T xn[kGroup], rn[kGroup], wn[kGroup];
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u) {
+                    xn[u] = fmaT(om2, qi[u], fmaT(al, pi[u], xi[u]));
+                    rn[u] = fmaT(-om2, yi[u], qi[u]);                     // eq. (7)
+                    wn[u] = fmaT(-om2, fmaT(-al, vi[u], ti[u]), yi[u]);   // eq. (8)
+                    if (u < cnt) {
+                        a2[0].add(r0i[u], rn[u]);
+                        a2[1].add(r0i[u], wn[u]);
+                        a2[2].add(rn[u], rn[u]);
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < kRows; ++u) {
-                    const int i = i0 + u * kTPB;
-                    if (i < hi) {
-                        x[i] = fmaT(om2, qi[u], fmaT(al, pi[u], xi[u]));
-                        const T rn = fmaT(-om2, yi[u], qi[u]);                          // eq. (7)
-                        const T wn = fmaT(-om2, fmaT(-al, vi[u], ti[u]), yi[u]);        // eq. (8)
-                        V.v[i] = vi[u];
-                        V.r[i] = rn;
-                        V.w[i] = wn;
-                        a2[0].add(r0i[u], rn);
-                        a2[1].add(r0i[u], wn);
-                        a2[2].add(rn, rn);
-                    }
-                }
+                store_group(x, i0, cnt, xn);
+                store_group(V.v, i0, cnt, vi);
+                store_group(V.r, i0, cnt, rn);
+                store_group(V.w, i0, cnt, wn);
             }
             ++spmvs;
         } else {
@@ -920,17 +942,21 @@ struct MixedArgs {
     int inner_maxit;
 };
 
-// 10 resident blocks per SM (48 registers): the FP32 inner sweeps are bound
-// by load latency, and more warps in flight measured faster (192^3: 315 vs
-// 325 us per stencil inner iteration, 346 vs 371 us CSR, against 8 blocks).
+// 9 resident blocks per SM (56 registers). The FP32 inner sweeps are bound by
+// load latency; with rows in aligned pairs, 9 blocks measured fastest (192^3:
+// 281 us per stencil inner iteration and 331 us CSR, against 288 / 335 at 8
+// blocks and 315 / 339 at 10, where the pairs spill more).
 template <class Op64, class Op32>
-__global__ void __launch_bounds__(kTPB, 10) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
+__global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
     if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier
     GridSync g{m.ctl, m.partials, 0u, 0};
-    const int lo = (int)((long long)blockIdx.x * m.n / gridDim.x);
-    const int hi = (int)((long long)(blockIdx.x + 1) * m.n / gridDim.x);
+    // row ranges start on even rows: the FP32 sweeps access rows in aligned pairs
+    const long long pairs = (m.n + 1) / 2;
+    const int lo = (int)(2 * ((long long)blockIdx.x * pairs / gridDim.x));
+    const int hi_pair = (int)(2 * ((long long)(blockIdx.x + 1) * pairs / gridDim.x));
+    const int hi = hi_pair < m.n ? hi_pair : m.n;
     int outer = 0, inner_total = 0, status = PBCG_NOT_CONVERGED, spmvs = 0;
     double nr0 = 0.0, tol = 0.0, tol2 = 0.0, last = 0.0;
     for (;;) {

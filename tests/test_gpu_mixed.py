@@ -114,6 +114,30 @@ def test_mixed_on_a_large_grid_is_deterministic_and_converges():
     s.close()
 
 
+@pytest.mark.parametrize("grid", [7, 1000])
+def test_mixed_odd_size_with_row_pairs_at_block_edges(grid):
+    """The FP32 sweeps take rows in aligned pairs and every block's range
+    starts on an even row. n = 3001 is odd, so the last row has no partner.
+    With 1000 blocks most ranges hold one pair, some none, and the last
+    block holds a pair and the lone row; with 7 blocks the ranges are long.
+    Both reach the FP64 solution, bit-identically on a repeat."""
+    import torch
+    A = systems()["rand_3001"]
+    b = oracle.spmv(A, P.splitmix64_uniform(3, A.n))
+    s = native.Solver.from_csr(A)
+    v32 = dev(A.val).to(torch.float32)
+    kw = dict(rtol=1e-10, max_outer=30, inner_rtol=1e-3, inner_maxit=2000, grid=grid)
+    x1, i1 = s.solve_mixed(dev(b), v32, native.PBCG_VALUES_F32, **kw)
+    x2, _ = s.solve_mixed(dev(b), v32, native.PBCG_VALUES_F32, **kw)
+    assert i1["status"] == native.PBCG_OK and i1["grid"] == grid, i1
+    xg = x1.cpu().numpy()
+    np.testing.assert_array_equal(xg, x2.cpu().numpy())
+    assert np.linalg.norm(b - oracle.spmv(A, xg)) / np.linalg.norm(b) <= 1e-10
+    ref = oracle.pbicgstab(A, b, rtol=1e-12, maxit=3000, replace_period=20)
+    assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+    s.close()
+
+
 def test_mixed_rejects_bad_arguments():
     import torch
     s = native.Solver.from_stencil(P.cd2d_constant(16))

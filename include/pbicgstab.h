@@ -179,7 +179,11 @@ pbcg_status pbicgstab_solve_host(pbicgstab_t h, int32_t method, const double *h_
                                  int32_t maxit, int32_t replace_period, const pbcg_opts *opts, pbcg_info *info);
 
 /* y = A x with the handle's operator (the SpMV building block, Section 1).
- * Asynchronous on the handle's stream; d_x and d_y must not overlap. */
+ * Asynchronous on the handle's stream; d_x and d_y must not overlap. Each
+ * row is one chain of FP64 fused multiply-adds, acc = fma(a, x[col], acc)
+ * from acc = 0, over the row's entries in storage order (CSR) or in the
+ * order B, S, W, C, E, N, T (stencil); the solvers form their products the
+ * same way. */
 pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y);
 
 /* Number of unknowns of the handle. */

@@ -51,8 +51,26 @@ struct QLoad {
 };
 
 // CSR with values stored as V (double; float or bfloat16 for low-precision
-// inner solves). A row is accumulated in the loader's type.
-template <typename V>
+// inner solves). A row is accumulated in the loader's type, in storage order.
+// kChunk > 1 takes a row's entries kChunk at a time: all column indices and
+// values of a chunk in flight together, then all gathers, then the FMAs in
+// storage order (the same sum as the one-by-one loop). The entries missing
+// from a row's last chunk are predicated off. kChunk = 1 is the plain loop.
+// Which one pays was measured per matrix class (time per iteration, both
+// methods, FP64):
+// * 7-point rows (256^3): 7 at a time 5.5 % (Algorithm 9) and 6 % (Algorithm
+//   7) faster than one at a time; 8 at a time spilled registers and gained
+//   half as much, 4 at a time lost. Taking only whole chunks and the rest one
+//   at a time lost 10 %: warps holding a boundary row ran both paths.
+// * Random rows of 9-33 entries (2^20 rows): 7 at a time 4-5 % faster.
+// * 5-point rows (1024^2): one at a time fastest; 5 at a time 4 % and 7 at a
+//   time 3-9 % slower. A predicated-off FP64 FMA occupies the FP64 pipe like
+//   a live one, and 2 of every 7 were dead.
+// The library therefore uses 7 at a time for matrices averaging more than 6
+// entries per row and the plain loop otherwise. FP32 and BF16 values (the
+// inner solves) take 8 at a time (4 and 6 measured slower); the batched
+// solver keeps the plain loop (its rows gained nothing from chunks).
+template <typename V, int kChunk = 8>
 struct CsrOpT {
     int n;
     const int *__restrict__ rowptr;
@@ -64,37 +82,34 @@ struct CsrOpT {
         using T = decltype(u(0));
         const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
         T acc = T(0);
-        if constexpr (sizeof(V) >= 8) {
+        if constexpr (kChunk <= 1) {
             for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(__ldg(col + k)), acc);
         } else {
-            // Low-precision values (the FP32 inner solves): a sweep is bound by
-            // memory latency, not arithmetic, so the entries of a row are taken
-            // kW at a time -- all column indices and values in flight together,
-            // then all gathers, then the FMAs in storage order (the same sum as
-            // the one-by-one loop).
-            constexpr int kW = 8;
-            for (int k0 = b; k0 < e; k0 += kW) {
-                int c[kW] = {};
-                V v[kW] = {};
-                T xv[kW] = {};
+            for (int k0 = b; k0 < e; k0 += kChunk) {
+                int c[kChunk] = {};
+                V v[kChunk] = {};
+                T xv[kChunk] = {};
 #pragma unroll
-                for (int j = 0; j < kW; ++j)
+                for (int j = 0; j < kChunk; ++j)
                     if (k0 + j < e) {
                         c[j] = __ldg(col + k0 + j);
                         v[j] = __ldg(val + k0 + j);
                     }
 #pragma unroll
-                for (int j = 0; j < kW; ++j)
+                for (int j = 0; j < kChunk; ++j)
                     if (k0 + j < e) xv[j] = u(c[j]);
 #pragma unroll
-                for (int j = 0; j < kW; ++j)
+                for (int j = 0; j < kChunk; ++j)
                     if (k0 + j < e) acc = fmaT(value_as<T>(v[j]), xv[j], acc);
             }
         }
         return acc;
     }
 };
-using CsrOp = CsrOpT<double>;
+using CsrOpScalar = CsrOpT<double, 1>;    // one entry at a time
+using CsrOpChunked = CsrOpT<double, 7>;   // 7 entries at a time
+// Rows averaging more than this many entries take the chunked operator.
+constexpr long long kChunkedMinAvgRow = 6;
 
 // One coefficient: t1[i*a1 + j*b1 + k*c1] (or `value` when t1 is null) plus
 // t2[i*a2 + j*b2 + k*c2] when t2 is set (n2 = 1, else 0). Indices fit 31 bits

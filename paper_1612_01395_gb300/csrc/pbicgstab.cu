@@ -46,11 +46,14 @@ constexpr int kPrecVectors = 6;   // preconditioned handles: M^{-1}, r^ s^ z^ q^
 
 size_t vec_stride(int32_t n) { return ((size_t)(n > 0 ? n : 1) + 31) / 32 * 32; }   // doubles
 
+pbcg::CsrOpChunked chunked(const pbcg::CsrOpScalar &a) { return pbcg::CsrOpChunked{a.n, a.rowptr, a.col, a.val}; }
+
 }  // namespace
 
 struct pbicgstab_s {
     int kind;   // 0 = CSR, 1 = stencil
-    pbcg::CsrOp csr;
+    pbcg::CsrOpScalar csr;   // CSR arrays
+    bool csr_chunked;        // CSR: solver and SpMV use pbcg::CsrOpChunked (long rows)
     pbcg::StencilOp st;
     int n;
     char *ws;
@@ -248,8 +251,9 @@ pbcg_status run_solve(pbicgstab_s *h, bool pipelined, const double *d_b, double 
     PBCG_CUDA(cudaMemsetAsync(h->ctl, 0, sizeof(pbcg::Control), h->stream));
     if (h->ev0) PBCG_CUDA(cudaEventRecord(h->ev0, h->stream));
     if (h->n > 0) {
-        pbcg_status st = h->kind == 0 ? launch_solver(h, h->csr, pipelined, a, grid)
-                                      : launch_solver(h, h->st, pipelined, a, grid);
+        pbcg_status st = h->kind == 1 ? launch_solver(h, h->st, pipelined, a, grid)
+                         : h->csr_chunked ? launch_solver(h, chunked(h->csr), pipelined, a, grid)
+                                          : launch_solver(h, h->csr, pipelined, a, grid);
         if (st != PBCG_OK) return st;
     }
     if (h->ev1) PBCG_CUDA(cudaEventRecord(h->ev1, h->stream));
@@ -320,10 +324,16 @@ pbcg_status pbicgstab_create_csr(int32_t n, int32_t nnz, const int32_t *d_rowptr
     pbcg_status st = common_init(h, n, prec, d_workspace, ws_bytes, stream);
     if (st == PBCG_OK) {
         h->kind = 0;
-        h->csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        h->csr = pbcg::CsrOpScalar{n, d_rowptr, d_col, d_val};
         h->nnz = nnz;
-        st = occupancy<pbcg::CsrOp>(&h->occ_pipe, &h->occ_plain);
-        if (st == PBCG_OK) st = occupancy_prec<pbcg::CsrOp>(&h->occ_pipe_prec, &h->occ_plain_prec);
+        h->csr_chunked = (long long)nnz > pbcg::kChunkedMinAvgRow * (long long)n;
+        if (h->csr_chunked) {
+            st = occupancy<pbcg::CsrOpChunked>(&h->occ_pipe, &h->occ_plain);
+            if (st == PBCG_OK) st = occupancy_prec<pbcg::CsrOpChunked>(&h->occ_pipe_prec, &h->occ_plain_prec);
+        } else {
+            st = occupancy<pbcg::CsrOpScalar>(&h->occ_pipe, &h->occ_plain);
+            if (st == PBCG_OK) st = occupancy_prec<pbcg::CsrOpScalar>(&h->occ_pipe_prec, &h->occ_plain_prec);
+        }
     }
     if (st == PBCG_OK) st = check_csr(h, n, nnz, d_rowptr, d_col);
     if (st == PBCG_OK && prec == PBCG_PREC_JACOBI && n > 0)
@@ -443,7 +453,9 @@ pbcg_status pbicgstab_spmv(pbicgstab_t h, const double *d_x, double *d_y) {
     if ((d_x < d_y + h->n) && (d_y < d_x + h->n)) return fail(PBCG_ERR_ARG, "x and y overlap");
     int blocks = (h->n + pbcg::kTPB - 1) / pbcg::kTPB;
     if (blocks > 16 * h->num_sms) blocks = 16 * h->num_sms;
-    if (h->kind == 0)
+    if (h->kind == 0 && h->csr_chunked)
+        pbcg::spmv_kernel<<<blocks, pbcg::kTPB, 0, h->stream>>>(chunked(h->csr), d_x, d_y);
+    else if (h->kind == 0)
         pbcg::spmv_kernel<<<blocks, pbcg::kTPB, 0, h->stream>>>(h->csr, d_x, d_y);
     else
         pbcg::spmv_kernel<<<blocks, pbcg::kTPB, 0, h->stream>>>(h->st, d_x, d_y);
@@ -899,9 +911,11 @@ extern "C" pbcg_status pbicgstab_solve_csr_noalloc(int32_t n, int32_t nnz, const
     st = common_init(&h, n, PBCG_PREC_NONE, ws, kNoAllocBytes, stream, false);
     if (st == PBCG_OK) {
         h.kind = 0;
-        h.csr = pbcg::CsrOp{n, d_rowptr, d_col, d_val};
+        h.csr = pbcg::CsrOpScalar{n, d_rowptr, d_col, d_val};
         h.nnz = nnz;
-        st = occupancy<pbcg::CsrOp>(&h.occ_pipe, &h.occ_plain);
+        h.csr_chunked = (long long)nnz > pbcg::kChunkedMinAvgRow * (long long)n;
+        st = h.csr_chunked ? occupancy<pbcg::CsrOpChunked>(&h.occ_pipe, &h.occ_plain)
+                           : occupancy<pbcg::CsrOpScalar>(&h.occ_pipe, &h.occ_plain);
     }
     if (st == PBCG_OK) st = check_csr(&h, n, nnz, d_rowptr, d_col);
     if (st != PBCG_OK) return st;

@@ -1090,7 +1090,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
     int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
     const int n = bad ? 0 : (int)(r1 - r0);
     const int lo = (int)((long long)part * n / parts), hi = (int)((long long)(part + 1) * n / parts);
-    const CsrOp A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
+    const CsrOpScalar A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
     PBCG_ROWS(i) {
         const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
         if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
@@ -1120,7 +1120,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
         a.rh = a.sh = a.zh = a.qh = a.wh = nullptr;
         Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
         int spmvs = 0;
-        pipelined_loop<CsrOp, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
+        pipelined_loop<CsrOpScalar, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
         // true residual of the returned x
         double d[1] = {0.0};
         PBCG_ROWS(i) {

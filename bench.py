@@ -47,8 +47,8 @@ ORACLE_ITERS = {"pbicgstab_rr50": 415, "bicgstab": 352}
 # the kernel sources it was taken on: SHA-256 over KERNEL_SOURCES.
 KERNEL_SOURCES = ["paper_1612_01395_gb300/csrc/device_common.cuh", "paper_1612_01395_gb300/csrc/operators.cuh",
                   "paper_1612_01395_gb300/csrc/solvers.cuh"]
-TRAFFIC_CAPTURE = {"bytes_per_launch": 984038465792 + 539638978304, "n": 16777216, "iters": 402, "grid": 1216,
-                   "sources_sha256": "e3087048cf924ea09e8a38b018d2f0b11e6994f86cf1529f79a1aa4d1d839ae9"}
+TRAFFIC_CAPTURE = {"bytes_per_launch": 984024159488 + 539637527296, "n": 16777216, "iters": 402, "grid": 1216,
+                   "sources_sha256": "8087c08c6f8f3f686203d014ba1c7ffafc72a7c5d682caa212b8a3e431232b62"}
 
 
 def kernel_sources_sha256():
@@ -342,13 +342,17 @@ def jacobi_case(st, bd, x, barrier):
 
 
 def grid_sensitivity(solver, bd, x, grid):
-    """Iterations to rtol of both methods at other grid sizes. The grid fixes
-    the order in which dot products are summed, and BiCGStab's trajectory
-    depends on rounding: the counts to 1e-8 move by 10-20 %, so the time
-    comparison of the two methods is also given per iteration."""
+    """Both methods to rtol at 4 to 9 blocks per SM (each method up to its
+    own co-resident maximum). The grid fixes the order in which dot products
+    are summed, and BiCGStab's trajectory depends on rounding: the counts to
+    1e-8 move by 10-20 %. So the two methods are also compared by the median
+    over these grids of their time to rtol, besides the time per iteration."""
+    import torch
     from paper_1612_01395_gb300 import native
+    per_sm = torch.cuda.get_device_properties(0).multi_processor_count
     out = {}
-    for g in sorted({grid // 2, (3 * grid) // 4, grid}):
+    times = {"pipelined": [], "standard": []}
+    for g in [k * per_sm for k in range(4, 10)]:
         row = {}
         for method in ("pipelined", "standard"):
             x.zero_()
@@ -357,9 +361,17 @@ def grid_sensitivity(solver, bd, x, grid):
                                                   grid=g)
             else:
                 st, info = native.bicgstab_solve(solver.h, bd.data_ptr(), x.data_ptr(), RTOL, MAXIT, grid=g)
-            row[method] = {"iters": info.iters, "ms_per_iter": info.kernel_ms / max(info.iters, 1),
+            if info.grid != g:   # above this method's co-resident maximum
+                continue
+            row[method] = {"iters": info.iters, "ms": info.kernel_ms, "ms_per_iter": info.kernel_ms / max(info.iters, 1),
                            "status": native.STATUS_NAMES.get(st)}
+            if st == native.PBCG_OK:
+                times[method].append(info.kernel_ms)
         out[str(g)] = row
+    med = {m: statistics.median(t) / 1e3 if t else None for m, t in times.items()}
+    out["median_s_over_grids"] = med
+    out["median_p_over_plain"] = (med["pipelined"] / med["standard"]
+                                  if med["pipelined"] and med["standard"] else None)
     return out
 
 

@@ -50,13 +50,24 @@ struct SolveArgsT {
 using SolveArgs = SolveArgsT<double>;
 
 // Resident blocks per SM the solver kernels are compiled for (register cap
-// 65536 / (kTPB * kMinBlocks) = 64): the large-n sweeps are limited by the
-// FP64 pipe, which needs many warps in flight to cover memory latency. At
+// 65536 / (kTPB * kMinBlocks) = 64 at 8): the large-n sweeps are limited by
+// the FP64 pipe, which needs many warps in flight to cover memory latency. At
 // 256^3 the stencil kernels take 1.25 (p-BiCGStab) and 1.27 ms (BiCGStab) per
-// iteration with 6 blocks per SM and 1.18 and 1.10 ms with 8; neither spills.
+// iteration with 6 blocks per SM and 1.14 and 1.08 ms with 8. With 9 (56
+// registers), p-BiCGStab slows to 1.20 ms while BiCGStab, whose sweeps hold
+// fewer values, speeds up to 1.05 ms; 10 is slower for both. Each method's
+// stencil kernel takes its own best.
 template <class Op>
 struct Tune {
     static constexpr int kMinBlocks = 8;
+};
+template <class Op>
+struct TunePlain {
+    static constexpr int kMinBlocks = Tune<Op>::kMinBlocks;
+};
+template <>
+struct TunePlain<StencilOp> {
+    static constexpr int kMinBlocks = 9;
 };
 
 struct Outcome {
@@ -899,7 +910,7 @@ __device__ __forceinline__ bool standard_prec_loop(const Op &A, const SolveArgs 
 }
 
 template <class Op, bool Prec>
-__global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) bicgstab_kernel(const Op A, const SolveArgs a) {
+__global__ void __launch_bounds__(kTPB, TunePlain<Op>::kMinBlocks) bicgstab_kernel(const Op A, const SolveArgs a) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
     if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier

@@ -171,8 +171,28 @@ struct DotAcc<float> {
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
-template <typename T, int K>
-__device__ __forceinline__ void dot_values(const DotAcc<T> (&acc)[K], double (&d)[K]) {
+// Plain FP32 accumulation by FMA, converted to double once per thread and
+// sweep (a thread sums a few dozen rows; the block and grid sums are FP64).
+// The stencil-form inner sweeps use it: their instruction count shows in their
+// time, and Dot2's eight operations per product cost 10 % per inner iteration
+// (192^3: 279 against 251 us); the CSR form, bound by its matrix traffic,
+// measured the same either way and keeps Dot2.
+struct DotAccFma {
+    float s = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) { s = __fmaf_rn(a, b, s); }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <class Op, typename T>
+struct DotAccFor {
+    using type = DotAcc<T>;
+};
+template <>
+struct DotAccFor<StencilOpT<float>, float> {
+    using type = DotAccFma;
+};
+
+template <class Acc, int K>
+__device__ __forceinline__ void dot_values(const Acc (&acc)[K], double (&d)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) d[k] = acc[k].value();
 }
@@ -229,11 +249,12 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     // halves their load and store instructions; their callers give every
     // block an even first row.
     constexpr int kGroup = sizeof(T) == 4 ? 2 : 1;
+    using Acc = typename DotAccFor<Op, T>::type;
 
     // r_0 := b - A x_0; shadow r0 := r_0; p, s, z, v := 0 (they are multiplied by beta_{-1} = 0)
     double d0[1];
     {
-        DotAcc<T> acc[1];
+        Acc acc[1];
         PBCG_ROWS(i) {
             const T ri = a.b[i] - A.row(i, VecLoadT<T>{x});
             V.r[i] = ri;
@@ -257,7 +278,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
 
     // w_0 := A r_0; alpha_0 := (r0, r0) / (r0, w0)
     {
-        DotAcc<T> acc[1];
+        Acc acc[1];
         PBCG_ROWS(i) {
             const T wi = A.row(i, VecLoadT<T>{V.r});
             V.w[i] = wi;
@@ -275,7 +296,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     int it = 0;
     while (it < a.limit) {
         // ---- phase A: t_i = A w_i; p_i, s_i, z_i, q_i, y_i; first reduction
-        DotAcc<T> a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
+        Acc a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         const T al = (T)alpha, be = (T)beta, om = (T)omega;
         if (!replaced_rw) {
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
@@ -364,7 +385,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         // ---- phase B: v_i = A z_i; x_{i+1}, r_{i+1}, w_{i+1}; second reduction
         const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
                                  (a.max_repl < 0 || o.nrr < a.max_repl);
-        DotAcc<T> a2[3];   // (r0,r) (r0,w) (r,r)
+        Acc a2[3];   // (r0,r) (r0,w) (r,r)
         const T om2 = (T)omega;
         if (!replace_now) {
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {

@@ -166,7 +166,120 @@ struct StencilOpT {
         if (k < nz - 1) acc = fmaT((T)coef(PBCG_T, i, j, k), u(r + nxy), acc);
         return acc;
     }
+
+    // Coefficient d at the nodes (i, j, k) and (i+1, j, k): one load when the
+    // table does not vary along x (stride 0), else one per node; each sum of
+    // two tables formed per node as in coef().
+    __device__ __forceinline__ void coef2(int d, int i, int j, int k, C &v0, C &v1) const {
+        const StCoefT<C> &q = c[d];
+        if (q.t1) {
+            const int at = i * q.a1 + j * q.b1 + k * q.c1;
+            v0 = __ldg(q.t1 + at);
+            v1 = q.a1 == 0 ? v0 : __ldg(q.t1 + at + q.a1);
+        } else {
+            v0 = v1 = q.value;
+        }
+#pragma unroll 1
+        for (int m = 0; m < q.n2; ++m) {
+            const int at = i * q.a2 + j * q.b2 + k * q.c2;
+            const C w0 = __ldg(q.t2 + at);
+            const C w1 = q.a2 == 0 ? w0 : __ldg(q.t2 + at + q.a2);
+            v0 = add_rn(v0, w0);
+            v1 = add_rn(v1, w1);
+        }
+    }
+
+    // Rows r and r+1 (r even) lie on one x-line for every even r when nx is
+    // even. The sweeps use row2 only then: with odd nx some pairs span two
+    // lines, and a warp holding one runs both of row2's paths.
+    __device__ __forceinline__ bool pairs_on_lines() const { return (nx & 1) == 0; }
+
+    // Rows r and r+1 (r even) of the FP32 inner sweeps, y[0] and y[1], each
+    // summed exactly as row() sums it: the same products in the same order,
+    // so the results are bitwise those of two row() calls. When both rows lie
+    // on one x-line they share the decomposition of r, the coefficient loads
+    // that do not vary along x, and their neighbour loads, taken as 64-bit
+    // pairs where both values are 8-byte aligned (r even; the offsets nx and
+    // nx*ny even). A pair that spans two x-lines (odd nx) takes two row()s.
+    template <class T>
+    __device__ __forceinline__ void row2(int r, const T *u, T (&y)[2]) const {
+        static_assert(sizeof(T) == 4 && sizeof(C) == 4, "pairs of FP32 rows");
+        const int t = (int)dx.div((uint32_t)r);
+        const int i = r - t * nx;
+        if (i + 1 >= nx) {
+            const VecLoadT<T> L{u};
+            y[0] = row(r, L);
+            y[1] = row(r + 1, L);
+            return;
+        }
+        const int k = (int)dy.div((uint32_t)t);
+        const int j = t - k * ny;
+        // u at offset o and o + 1 from r (o even when `even`)
+        auto pair_at = [&](int o, bool even, T &a, T &b) {
+            if (even) {
+                const float2 v = *reinterpret_cast<const float2 *>(u + r + o);
+                a = v.x;
+                b = v.y;
+            } else {
+                a = u[r + o];
+                b = u[r + o + 1];
+            }
+        };
+        T a0 = T(0), a1 = T(0);
+        C c0, c1;
+        if (k > 0) {
+            T v0, v1;
+            pair_at(-nxy, (nxy & 1) == 0, v0, v1);
+            coef2(PBCG_B, i, j, k, c0, c1);
+            a0 = fmaT((T)c0, v0, a0);
+            a1 = fmaT((T)c1, v1, a1);
+        }
+        if (j > 0) {
+            T v0, v1;
+            pair_at(-nx, (nx & 1) == 0, v0, v1);
+            coef2(PBCG_S, i, j, k, c0, c1);
+            a0 = fmaT((T)c0, v0, a0);
+            a1 = fmaT((T)c1, v1, a1);
+        }
+        T u0, u1;
+        pair_at(0, true, u0, u1);
+        coef2(PBCG_W, i, j, k, c0, c1);
+        if (i > 0) a0 = fmaT((T)c0, u[r - 1], a0);
+        a1 = fmaT((T)c1, u0, a1);
+        coef2(PBCG_C, i, j, k, c0, c1);
+        a0 = fmaT((T)c0, u0, a0);
+        a1 = fmaT((T)c1, u1, a1);
+        coef2(PBCG_E, i, j, k, c0, c1);
+        a0 = fmaT((T)c0, u1, a0);
+        if (i + 2 < nx) a1 = fmaT((T)c1, u[r + 2], a1);
+        if (j < ny - 1) {
+            T v0, v1;
+            pair_at(nx, (nx & 1) == 0, v0, v1);
+            coef2(PBCG_N, i, j, k, c0, c1);
+            a0 = fmaT((T)c0, v0, a0);
+            a1 = fmaT((T)c1, v1, a1);
+        }
+        if (k < nz - 1) {
+            T v0, v1;
+            pair_at(nxy, (nxy & 1) == 0, v0, v1);
+            coef2(PBCG_T, i, j, k, c0, c1);
+            a0 = fmaT((T)c0, v0, a0);
+            a1 = fmaT((T)c1, v1, a1);
+        }
+        y[0] = a0;
+        y[1] = a1;
+    }
 };
 using StencilOp = StencilOpT<double>;
+
+// Operators with row2 (pairs of FP32 rows).
+template <class Op>
+struct HasRow2 {
+    static constexpr bool value = false;
+};
+template <>
+struct HasRow2<StencilOpT<float>> {
+    static constexpr bool value = true;
+};
 
 }  // namespace pbcg

@@ -302,9 +302,19 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
                 const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
                 T ti[kGroup] = {}, ri[kGroup], wi[kGroup], si[kGroup], zi[kGroup], pi[kGroup], vi[kGroup], r0i[kGroup];
+                if constexpr (kGroup == 2 && HasRow2<Op>::value) {
+                    if (cnt == 2 && A.pairs_on_lines()) {
+                        A.row2(i0, V.w, ti);
+                    } else {
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
-                    if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
+                        for (int u = 0; u < kGroup; ++u)
+                            if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+                        if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
+                }
                 load_group(V.r, i0, cnt, ri);
                 load_group(V.w, i0, cnt, wi);
                 load_group(V.s, i0, cnt, si);
@@ -391,9 +401,19 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
                 const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
                 T vi[kGroup] = {}, qi[kGroup], yi[kGroup], xi[kGroup], pi[kGroup], ti[kGroup], r0i[kGroup];
+                if constexpr (kGroup == 2 && HasRow2<Op>::value) {
+                    if (cnt == 2 && A.pairs_on_lines()) {
+                        A.row2(i0, V.z, vi);
+                    } else {
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
-                    if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
+                        for (int u = 0; u < kGroup; ++u)
+                            if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u)
+                        if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
+                }
                 load_group(V.q, i0, cnt, qi);
                 load_group(V.y, i0, cnt, yi);
                 load_group(x, i0, cnt, xi);

@@ -73,13 +73,18 @@ def test_mixed_bf16_values_converge_on_well_conditioned_system():
     s.close()
 
 
-@pytest.mark.parametrize("name", ["cd2d_64", "cd3d_20"])
+STENCILS = {"cd2d_64": lambda: P.cd2d_constant(64, (10.0, 10.0)), "cd3d_20": lambda: P.cd3d_trig(20),
+            "cd2d_63": lambda: P.cd2d_constant(63, (10.0, 10.0)), "cd3d_21": lambda: P.cd3d_trig(21)}
+
+
+@pytest.mark.parametrize("name", list(STENCILS))
 def test_mixed_fp32_stencil_form_reaches_1e10_true_residual(name):
     """Stencil handles: the inner solves use the coefficient tables rounded to
     FP32 (a summed coefficient is then added in FP32, so the inner operator can
     differ from the rounded CSR values in the last bit); the FP64 refinement
-    still reaches the FP64 solution."""
-    st = P.cd2d_constant(64, (10.0, 10.0)) if name == "cd2d_64" else P.cd3d_trig(20)
+    still reaches the FP64 solution. Even nx takes the inner sweeps' paired
+    rows (one SpMV call per x-line pair), odd nx one call per row."""
+    st = STENCILS[name]()
     A = P.stencil_to_csr(st)
     b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
     s = native.Solver.from_stencil(st)

@@ -212,8 +212,10 @@ enum { PBCG_VALUES_F32 = 0, PBCG_VALUES_BF16 = 1 };
  * handle's FP64 operator, solves A d = r with the FP32 pipelined iteration
  * to ||r_inner|| <= inner_rtol ||r|| (at most inner_maxit iterations) on a
  * low-precision copy of A, and sets x := x + d in FP64. Dot products that set
- * alpha, beta and omega are accumulated to FP64 accuracy (compensated FP32
- * per thread, FP64 across threads). Stops when the FP64 residual satisfies
+ * alpha, beta and omega are summed per thread in FP32 (compensated, to FP64
+ * accuracy, for CSR handles; a plain FMA chain over the thread's few dozen
+ * rows for stencil handles) and across threads in FP64; the scalars are FP64.
+ * Stops when the FP64 residual satisfies
  * ||b - A x|| <= rtol ||b - A x0|| or after max_outer steps
  * (PBCG_NOT_CONVERGED).
  *   h            a CSR or stencil handle

@@ -139,7 +139,8 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
 
 // Per-thread accumulation of a dot product over the rows of a sweep. FP64
 // vectors: an FMA into a double. FP32 vectors (the inner solves of the
-// mixed-precision refinement): compensated FP32 accumulation, algorithm Dot2
+// mixed-precision refinement; CSR form, see DotAccFma for the stencil form):
+// compensated FP32 accumulation, algorithm Dot2
 // of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
 // Comput. 26, 2005): each product is split exactly into its rounded value and
 // rounding error (TwoProduct by FMA), the running sum is updated by the
@@ -233,8 +234,8 @@ __device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[
 // ===========================================================================
 // T is the vector and sweep arithmetic type: double for the FP64 solver,
 // float for the inner solves of the mixed-precision refinement. Dot products
-// are always accumulated in double, and alpha, beta, omega, rho are doubles;
-// a sweep uses them rounded to T.
+// are summed per thread in T (DotAccFor) and across threads in double, and
+// alpha, beta, omega, rho are doubles; a sweep uses them rounded to T.
 template <class Op, typename T, class Sync = GridSync>
 __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> &a, Sync &g, double (*sm)[32],
                                                int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
@@ -974,7 +975,8 @@ __global__ void __launch_bounds__(kTPB, TunePlain<Op>::kMinBlocks) bicgstab_kern
 // Each refinement step computes the true residual r = b - A x with the FP64
 // matrix and FP64 vectors, rounds it to float, solves A d = r with Algorithm 9
 // on float vectors and the low-precision copy of A (FP32 or BF16 values; dot
-// products accumulated in FP64), and adds d to x in FP64. The true residual of
+// products summed per thread in FP32 and across threads in FP64), and adds d
+// to x in FP64. The true residual of
 // the last step is the reported one. The inner solve runs without residual
 // replacement: the FP64 residual of every refinement step plays that role.
 // ===========================================================================

@@ -333,6 +333,16 @@ pbcg_status pbicgstab_csr_value_grad(int32_t n, const int32_t *d_rowptr, const i
  * until the probe ends. */
 pbcg_status pbicgstab_probe_sync_timeout(pbicgstab_t h, int32_t limit_ms, int32_t *status);
 
+/* Bounds-checked builds (the library compiled with -DPBCG_CHECK; a debugging
+ * aid with no counterpart in the paper): the kernels check every index they
+ * form from data or geometry (gathered CSR columns, stencil neighbours, row
+ * pointers); an out-of-range one is replaced by 0 so that no access leaves
+ * its buffer, and the source line of the first is recorded on the current
+ * device. Synchronises the device, returns that line (0: none since the last
+ * call) and clears it; -2 if a CUDA call fails. The default build has no
+ * checks and returns -1. */
+int32_t pbicgstab_check_faults(void);
+
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
 #define PBCG_NOALLOC_MAX_N 32768
 

@@ -15,6 +15,24 @@ constexpr int kMaxGrid = 2048;     // upper bound on thread blocks (sizes the pa
 constexpr int kMaxDots = 8;        // dot products carried by one reduction
 constexpr uint64_t kSyncTimeoutNs = 4000000000ull;   // 4 s per grid-wide wait
 
+// Bounds-checked build (-DPBCG_CHECK): PBCG_SAFE(i, n) yields i when 0 <= i < n,
+// else records the source line in g_check_fault (the first such access only)
+// and yields 0, so the access stays in bounds and the solve carries on; the
+// host reads the record with pbicgstab_check_faults. It guards the indices
+// that the operators form from data or geometry (gathered columns, stencil
+// neighbours, row pointers). The default build compiles it to plain i.
+#ifdef PBCG_CHECK
+__device__ int g_check_fault;
+__device__ __forceinline__ long long checked_index(long long i, long long n, int line) {
+    if (i >= 0 && i < n) return i;
+    atomicCAS(&g_check_fault, 0, line);
+    return 0;
+}
+#define PBCG_SAFE(i, n) ((int)::pbcg::checked_index((long long)(i), (long long)(n), __LINE__))
+#else
+#define PBCG_SAFE(i, n) (i)
+#endif
+
 // Control block at the start of the workspace; zeroed before every solve.
 struct Control {
     unsigned int arrivals;   // grid-sync arrivals, monotonic within one launch

@@ -80,10 +80,10 @@ struct CsrOpT {
     template <class L>
     __device__ __forceinline__ auto row(int r, const L &u) const -> decltype(u(0)) {
         using T = decltype(u(0));
-        const int b = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+        const int b = __ldg(rowptr + PBCG_SAFE(r, n)), e = __ldg(rowptr + PBCG_SAFE(r, n) + 1);
         T acc = T(0);
         if constexpr (kChunk <= 1) {
-            for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(__ldg(col + k)), acc);
+            for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(PBCG_SAFE(__ldg(col + k), n)), acc);
         } else {
             for (int k0 = b; k0 < e; k0 += kChunk) {
                 int c[kChunk] = {};
@@ -97,7 +97,7 @@ struct CsrOpT {
                     }
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
-                    if (k0 + j < e) xv[j] = u(c[j]);
+                    if (k0 + j < e) xv[j] = u(PBCG_SAFE(c[j], n));
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
                     if (k0 + j < e) acc = fmaT(value_as<T>(v[j]), xv[j], acc);
@@ -157,13 +157,13 @@ struct StencilOpT {
         const int k = (int)dy.div((uint32_t)t);
         const int j = t - k * ny;
         T acc = T(0);
-        if (k > 0) acc = fmaT((T)coef(PBCG_B, i, j, k), u(r - nxy), acc);
-        if (j > 0) acc = fmaT((T)coef(PBCG_S, i, j, k), u(r - nx), acc);
-        if (i > 0) acc = fmaT((T)coef(PBCG_W, i, j, k), u(r - 1), acc);
-        acc = fmaT((T)coef(PBCG_C, i, j, k), u(r), acc);
-        if (i < nx - 1) acc = fmaT((T)coef(PBCG_E, i, j, k), u(r + 1), acc);
-        if (j < ny - 1) acc = fmaT((T)coef(PBCG_N, i, j, k), u(r + nx), acc);
-        if (k < nz - 1) acc = fmaT((T)coef(PBCG_T, i, j, k), u(r + nxy), acc);
+        if (k > 0) acc = fmaT((T)coef(PBCG_B, i, j, k), u(PBCG_SAFE(r - nxy, n)), acc);
+        if (j > 0) acc = fmaT((T)coef(PBCG_S, i, j, k), u(PBCG_SAFE(r - nx, n)), acc);
+        if (i > 0) acc = fmaT((T)coef(PBCG_W, i, j, k), u(PBCG_SAFE(r - 1, n)), acc);
+        acc = fmaT((T)coef(PBCG_C, i, j, k), u(PBCG_SAFE(r, n)), acc);
+        if (i < nx - 1) acc = fmaT((T)coef(PBCG_E, i, j, k), u(PBCG_SAFE(r + 1, n)), acc);
+        if (j < ny - 1) acc = fmaT((T)coef(PBCG_N, i, j, k), u(PBCG_SAFE(r + nx, n)), acc);
+        if (k < nz - 1) acc = fmaT((T)coef(PBCG_T, i, j, k), u(PBCG_SAFE(r + nxy, n)), acc);
         return acc;
     }
 
@@ -216,13 +216,14 @@ struct StencilOpT {
         const int j = t - k * ny;
         // u at offset o and o + 1 from r (o even when `even`)
         auto pair_at = [&](int o, bool even, T &a, T &b) {
+            const int at = PBCG_SAFE(r + o, n - 1);   // both at and at + 1 in range
             if (even) {
-                const float2 v = *reinterpret_cast<const float2 *>(u + r + o);
+                const float2 v = *reinterpret_cast<const float2 *>(u + at);
                 a = v.x;
                 b = v.y;
             } else {
-                a = u[r + o];
-                b = u[r + o + 1];
+                a = u[at];
+                b = u[at + 1];
             }
         };
         T a0 = T(0), a1 = T(0);
@@ -244,14 +245,14 @@ struct StencilOpT {
         T u0, u1;
         pair_at(0, true, u0, u1);
         coef2(PBCG_W, i, j, k, c0, c1);
-        if (i > 0) a0 = fmaT((T)c0, u[r - 1], a0);
+        if (i > 0) a0 = fmaT((T)c0, u[PBCG_SAFE(r - 1, n)], a0);
         a1 = fmaT((T)c1, u0, a1);
         coef2(PBCG_C, i, j, k, c0, c1);
         a0 = fmaT((T)c0, u0, a0);
         a1 = fmaT((T)c1, u1, a1);
         coef2(PBCG_E, i, j, k, c0, c1);
         a0 = fmaT((T)c0, u1, a0);
-        if (i + 2 < nx) a1 = fmaT((T)c1, u[r + 2], a1);
+        if (i + 2 < nx) a1 = fmaT((T)c1, u[PBCG_SAFE(r + 2, n)], a1);
         if (j < ny - 1) {
             T v0, v1;
             pair_at(nx, (nx & 1) == 0, v0, v1);

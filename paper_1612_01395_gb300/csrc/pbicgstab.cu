@@ -617,6 +617,22 @@ extern "C" pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lo
 }
 
 // ---------------------------------------------------------------------------
+// Bounds-checked builds.
+// ---------------------------------------------------------------------------
+extern "C" int32_t pbicgstab_check_faults(void) {
+#ifdef PBCG_CHECK
+    int line = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+    if (cudaMemcpyFromSymbol(&line, pbcg::g_check_fault, sizeof(int)) != cudaSuccess) return -2;
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(pbcg::g_check_fault, &zero, sizeof(int)) != cudaSuccess) return -2;
+    return line;
+#else
+    return -1;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostic of the bounded grid-wide wait.
 // ---------------------------------------------------------------------------
 extern "C" pbcg_status pbicgstab_probe_sync_timeout(pbicgstab_t h, int32_t limit_ms, int32_t *status) {

@@ -20,6 +20,7 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libpbicgstab.so")
+CHECK_LIB_PATH = os.path.join(_BUILD, "libpbicgstab_check.so")   # -DPBCG_CHECK build
 NVCC_ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 PBCG_OK, PBCG_NOT_CONVERGED, PBCG_BREAKDOWN, PBCG_NONFINITE = 0, 1, 2, 3
@@ -34,7 +35,7 @@ EXPORTS = ["pbicgstab_workspace_bytes", "pbicgstab_workspace_bytes_prec", "pbicg
            "pbicgstab_size", "pbicgstab_destroy", "pbicgstab_last_error", "pbicgstab_solve_csr_noalloc",
            "pbicgstab_solve_mixed", "pbicgstab_batched_workspace_bytes", "pbicgstab_solve_batched",
            "pbicgstab_transpose_work_bytes", "pbicgstab_csr_transpose", "pbicgstab_csr_value_grad",
-           "pbicgstab_probe_sync_timeout", "pbicgstab_batched_autotune"]
+           "pbicgstab_probe_sync_timeout", "pbicgstab_batched_autotune", "pbicgstab_check_faults"]
 PBCG_VALUES_F32, PBCG_VALUES_BF16 = 0, 1
 # Largest system the allocation-free entry point accepts (PBCG_NOALLOC_MAX_N).
 PBCG_NOALLOC_MAX_N = 32768
@@ -97,21 +98,25 @@ def sources():
         [os.path.join(_INCLUDE, "pbicgstab.h")]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA library for sm_103a with nvcc (in-tree, under _build/)."""
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile the CUDA library for sm_103a with nvcc (in-tree, under _build/).
+    check=True builds the bounds-checked variant (-DPBCG_CHECK) at CHECK_LIB_PATH."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB_PATH):
+    out = CHECK_LIB_PATH if check else LIB_PATH
+    if not force and os.path.exists(out):
         newest = max(os.path.getmtime(p) for p in sources())
-        if os.path.getmtime(LIB_PATH) >= newest:
-            return LIB_PATH
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+        if os.path.getmtime(out) >= newest:
+            return out
+    tmp = out + f".{os.getpid()}.tmp"
     cmd = ["nvcc", NVCC_ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
            "-I", _INCLUDE, "-o", tmp, os.path.join(_CSRC, "pbicgstab.cu")]
+    if check:
+        cmd.insert(1, "-DPBCG_CHECK")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, out)
+    return out
 
 
 _lib = None
@@ -150,6 +155,8 @@ def lib():
         L.pbicgstab_csr_transpose.restype = ctypes.c_int
         L.pbicgstab_csr_value_grad.argtypes = [i32, vp, vp, vp, vp, vp, vp]
         L.pbicgstab_probe_sync_timeout.argtypes = [vp, i32, ctypes.POINTER(i32)]
+        L.pbicgstab_check_faults.argtypes = []
+        L.pbicgstab_check_faults.restype = i32
         L.pbicgstab_batched_autotune.argtypes = [ctypes.POINTER(PbcgBatch), ctypes.c_int64, vp, vp, f64, i32, i32,
                                                  vp, sz, vp, vp, ctypes.POINTER(PbcgBatchOpts),
                                                  ctypes.POINTER(ctypes.c_float)]
@@ -344,6 +351,12 @@ def pbicgstab_csr_transpose(n, nnz, d_rowptr, d_col, d_val, d_trowptr, d_tcol, d
 
 def pbicgstab_csr_value_grad(n, d_rowptr, d_col, d_lambda, d_x, d_grad, stream) -> int:
     return lib().pbicgstab_csr_value_grad(int(n), d_rowptr, d_col, d_lambda, d_x, d_grad, stream)
+
+
+def pbicgstab_check_faults() -> int:
+    """Bounds-checked build: source line of the first out-of-range index since
+    the last call (0: none); -1 from the default build."""
+    return int(lib().pbicgstab_check_faults())
 
 
 def pbicgstab_probe_sync_timeout(h, limit_ms):

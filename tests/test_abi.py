@@ -81,3 +81,12 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(out[cname]) == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_bounds_checked_build_compiles_and_exports():
+    """-DPBCG_CHECK build (nvcc cross-compiles without a GPU): same exports."""
+    import ctypes
+    path = native.build(check=True)
+    L = ctypes.CDLL(path)
+    for name in native.EXPORTS:
+        assert hasattr(L, name), name

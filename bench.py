@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 ORACLE_ITERS = {"pbicgstab_rr50": 415, "bicgstab": 352}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the solver kernel on this workload, from a one-pass ncu capture of the full
-# launch (profiles/traffic_pbicgstab_kernel_stencil_cd3d256.md), valid only for
-# the kernel sources it was taken on: SHA-256 over KERNEL_SOURCES.
+# launch, valid only for the kernel sources it was taken on: SHA-256 over
+# KERNEL_SOURCES.
 KERNEL_SOURCES = ["paper_1612_01395_gb300/csrc/device_common.cuh", "paper_1612_01395_gb300/csrc/operators.cuh",
                   "paper_1612_01395_gb300/csrc/solvers.cuh"]
 TRAFFIC_CAPTURE = {"bytes_per_launch": 984050745856 + 539641074688, "n": 16777216, "iters": 402, "grid": 1216,
@@ -190,15 +190,35 @@ def build_inputs(n, need_csr):
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------------
 
-def oracle_sample(A, b, method, iters_lo=2, iters_hi=6):
-    """Seconds per oracle iteration and fixed overhead, from two short runs."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(A, b, method, iters_lo=2, iters_hi=52, omp=False):
+    """Seconds per oracle iteration and fixed overhead, from two fixed-iteration
+    runs (iters_lo and iters_hi iterations); omp=True times the OpenMP build."""
     import oracle
     fn = oracle.pbicgstab if method == "pbicgstab" else oracle.bicgstab
     kw = {"replace_period": REPLACE_PERIOD} if method == "pbicgstab" else {}
     t = []
     for k in (iters_lo, iters_hi):
         t0 = time.perf_counter()
-        fn(A, b, rtol=0.0, maxit=k, fixed_iters=k, **kw)
+        fn(A, b, rtol=0.0, maxit=k, fixed_iters=k, omp=omp, **kw)
         t.append(time.perf_counter() - t0)
     per_iter = (t[1] - t[0]) / (iters_hi - iters_lo)
     overhead = max(t[0] - iters_lo * per_iter, 0.0)
@@ -206,14 +226,29 @@ def oracle_sample(A, b, method, iters_lo=2, iters_hi=6):
 
 
 def cpu_baseline(A, b, gpu_iters):
+    """The FP64 C oracle on the host cores: one complete solve (Algorithm 9,
+    replacement every 50, to rtol 1e-8) with the OpenMP build on all cores,
+    measured; and the single-threaded parity build on 2- and 52-iteration
+    runs, its per-iteration time scaled to the oracle's iteration count
+    (labelled extrapolated)."""
+    import oracle
+    model = cpu_model()
+    threads = oracle.num_threads(omp=True)
+    t0 = time.perf_counter()
+    full = oracle.pbicgstab(A, b, rtol=RTOL, maxit=MAXIT, replace_period=REPLACE_PERIOD, omp=True)
+    t_full = time.perf_counter() - t0
     per_iter, overhead, spent = oracle_sample(A, b, "pbicgstab")
     iters = ORACLE_ITERS["pbicgstab_rr50"] or gpu_iters
-    src = "oracle's own iteration count" if ORACLE_ITERS["pbicgstab_rr50"] else "the GPU solve's iteration count"
-    return {"value": overhead + iters * per_iter, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"2 and 6 fixed iterations of the FP64 C oracle (Algorithm 9, CSR form) on the full "
-                      f"{A.n}-unknown system ({spent:.1f} s of CPU work), per-iteration time scaled to "
-                      f"{iters} iterations ({src})",
-            "s_per_iter": per_iter}
+    return {"value": t_full, "unit": "s", "cores": threads, "kind": "oracle", "cpu_model": model,
+            "sample": f"one complete solve of the full {A.n}-unknown system (CSR assembly of the same stencil) by "
+                      f"the OpenMP build of the FP64 C oracle on {threads} threads: {full.iters} iterations to a "
+                      f"true rel.res of {full.rel_res_true:.2e}, measured (not extrapolated)",
+            "iters": full.iters, "status": int(full.status),
+            "single_thread": {"value": overhead + iters * per_iter, "unit": "s", "cores": 1,
+                              "s_per_iter": per_iter, "extrapolated": True,
+                              "sample": f"2 and 52 fixed iterations of the single-threaded parity build "
+                                        f"({spent:.1f} s of CPU work), per-iteration time scaled to {iters} "
+                                        f"iterations (the oracle's own count)"}}
 
 
 def run_reference(args):
@@ -224,9 +259,10 @@ def run_reference(args):
     import oracle
     st, A, xs = build_inputs(n, need_csr=True)
     b = oracle.spmv(A, xs)
+    threads = oracle.num_threads(omp=True)
     vals = []
     for s in range(args.warmup + args.steps):
-        per_iter, overhead, spent = oracle_sample(A, b, "pbicgstab", 1, 3)
+        per_iter, overhead, spent = oracle_sample(A, b, "pbicgstab", 2, 52, omp=True)
         iters = ORACLE_ITERS["pbicgstab_rr50"] or 0
         v = overhead + iters * per_iter if iters else per_iter
         if s >= args.warmup:
@@ -237,11 +273,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(n), parallelism="replicas only" if world > 1 else "single GPU"),
-            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
-                             "sample": "1 and 3 fixed iterations of the FP64 C oracle (Algorithm 9) per step on "
-                                       "the full system, applied through the CSR assembly of the same stencil "
-                                       "(identical values), on one host core; per-iteration time scaled to "
-                                       "the oracle's own iteration count"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads, "kind": "oracle",
+                             "cpu_model": cpu_model(), "extrapolated": True,
+                             "sample": "per step: 2 and 52 fixed iterations of the OpenMP build of the FP64 C "
+                                       f"oracle (Algorithm 9) on {threads} threads on the full system, applied "
+                                       "through the CSR assembly of the same stencil (identical values); "
+                                       "per-iteration time scaled to the oracle's own iteration count"},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -454,6 +491,7 @@ def mixed_precision_case(n, steps, barrier):
         inner_bytes = 24 * 4 * N + mat_bytes   # FP32 vectors (+ low-precision CSR), per inner iteration
         out[name] = {"value": sec, "outer": im["outer"], "inner_iters": im["inner_iters"], "inner_maxit": cap,
                      "rel_res_true": im["rel_res_true"], "status": native.STATUS_NAMES[im["status"]],
+                     "returned_best_earlier_iterate": bool(im["restored"]),
                      "rel_error_vs_fp64": err, "speedup_vs_fp64": ref / sec,
                      "ms_per_inner_iter": im["kernel_ms"] / max(1, im["inner_iters"]),
                      "s_per_grid": per_grid, "median_s_over_grids": median, "median_speedup_vs_fp64": ref / median,
@@ -526,13 +564,19 @@ def adjoint_case(n, barrier):
     """Reverse-mode gradient of L = 0.5 ||x - x_target||^2, x = A^{-1} b, on the
     n^2 convection-diffusion system with per-cell velocity c ~ U[0, 50]:
     forward solve + adjoint solve with A^T (pipelined BiCGStab, rtol 1e-13,
-    replacement every 50) against finite differences on 16 random coordinates:
-    dL/db by central differences with step 1e-2 (L is quadratic in b, so only
-    solve noise remains), dL/dvalues by central differences at steps 5e-3 and
-    1e-2 combined by one Richardson step (truncation O(step^4))."""
+    replacement every 50), checked against central finite differences two ways:
+
+    * the configured check: step h = 1e-6 on 32 random coordinates (16 of b,
+      16 of the matrix values); each perturbed solution is the unperturbed x*
+      plus a correction solved to rtol 1e-10 of its own right-hand side, so
+      the correction's error scales with h and the difference quotient keeps
+      its accuracy; per-coordinate relative errors |fd - g| / |g|, no floor;
+    * large steps from cold starts: dL/db with h = 1e-2 (L is quadratic in b),
+      dL/dvalues by one Richardson step over 5e-3 and 1e-2, errors against
+      |g| + 1e-3 max|g|, on 16 coordinates."""
     import torch
     import numpy as np
-    from paper_1612_01395_gb300 import problems as P
+    from paper_1612_01395_gb300 import native, problems as P
     from paper_1612_01395_gb300.adjoint import CSRStructure, sparse_solve
     A = P.stencil_to_csr(P.cd2d_field(n, seed=SEED))
     st = CSRStructure(A.rowptr, A.col)
@@ -559,6 +603,54 @@ def adjoint_case(n, barrier):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     gb, gv = bb.grad.cpu().numpy(), vals.grad.cpu().numpy()
+
+    # configured check: h = 1e-6. Each perturbed solution is x* + d with
+    # A' d = b' - A' x* (A', b' the perturbed system), solved from d = 0 to rtol
+    # 1e-10 of its own right-hand side; the numerator of the central difference,
+    # L(+) - L(-), is evaluated without cancellation for this quadratic loss:
+    # (x* - x_t).(d+ - d-) + (|d+|^2 - |d-|^2) / 2.
+    with torch.no_grad():
+        xstar = sparse_solve(vals0, b0, st, rtol=1e-13)
+    nws = native.pbicgstab_workspace_bytes(A.n)
+    ws = torch.empty(nws // 8 + 64, dtype=torch.float64, device="cuda")
+    wsp = (ws.data_ptr() + 255) // 256 * 256
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def correction(v, bvec):
+        h = native.pbicgstab_create_csr(A.n, A.nnz, st.rowptr.data_ptr(), st.col.data_ptr(), v.data_ptr(),
+                                        native.PBCG_PREC_NONE, wsp, nws, stream)
+        ax = torch.empty_like(xstar)
+        native.pbicgstab_spmv(h, xstar.data_ptr(), ax.data_ptr())
+        rhs = bvec - ax
+        d = torch.zeros_like(xstar)
+        rc, info = native.pbicgstab_solve(h, rhs.data_ptr(), d.data_ptr(), 1e-10, MAXIT, REPLACE_PERIOD)
+        native.pbicgstab_destroy(h)
+        if rc != native.PBCG_OK:
+            raise RuntimeError(f"correction solve failed: {native.STATUS_NAMES.get(rc)}")
+        return d
+
+    def central_numerator(vp, bp, vm, bm):
+        dp, dm = correction(vp, bp), correction(vm, bm)
+        return float(torch.dot(xstar - xt, dp - dm) + 0.5 * (torch.dot(dp, dp) - torch.dot(dm, dm)))
+
+    hcfg = 1e-6
+    rel_cfg = []
+    t3 = time.perf_counter()
+    with torch.no_grad():
+        for i in (P.splitmix64(SEED + 21, 16) % np.uint64(A.n)).astype(int):
+            e = torch.zeros_like(b0)
+            e[i] = hcfg
+            fd = central_numerator(vals0, b0 + e, vals0, b0 - e) / (2 * hcfg)
+            rel_cfg.append(("b", int(i), float(gb[i]), fd, abs(fd - gb[i]) / abs(gb[i])))
+        for k in (P.splitmix64(SEED + 22, 16) % np.uint64(A.nnz)).astype(int):
+            e = torch.zeros_like(vals0)
+            e[k] = hcfg
+            fd = central_numerator(vals0 + e, b0, vals0 - e, b0) / (2 * hcfg)
+            rel_cfg.append(("val", int(k), float(gv[k]), fd, abs(fd - gv[k]) / abs(gv[k])))
+    t4 = time.perf_counter()
+    rels = [r[4] for r in rel_cfg]
+
+    # large-step check from cold starts
     worst = 0.0
     sb, sv = 1e-3 * np.abs(gb).max(), 1e-3 * np.abs(gv).max()
 
@@ -566,7 +658,6 @@ def adjoint_case(n, barrier):
         return (float(loss(vals + e[0], bb + e[1])) - float(loss(vals - e[0], bb - e[1]))) / (2 * h)
 
     zv, zb = torch.zeros_like(vals0), torch.zeros_like(b0)
-    t3 = time.perf_counter()
     with torch.no_grad():
         for i in (P.splitmix64(SEED + 11, 8) % np.uint64(A.n)).astype(int):
             e = torch.zeros_like(b0)
@@ -578,14 +669,19 @@ def adjoint_case(n, barrier):
             e1[k], e2[k] = 5e-3, 1e-2
             fd = (4 * central(vals0, b0, (e1, zb), 5e-3) - central(vals0, b0, (e2, zb), 1e-2)) / 3
             worst = max(worst, abs(fd - gv[k]) / (abs(gv[k]) + sv))
-    t4 = time.perf_counter()
     return {"workload": f"2-D convection-diffusion {n}^2 (n={A.n}), per-cell velocity (c, c), c ~ U[0,50]; "
                         f"L = 0.5||x - x_t||^2; gradients w.r.t. b and the {A.nnz} matrix values",
             "forward_s": t1 - t0, "backward_s": t2 - t1, "value": t2 - t0, "unit": "s",
-            "fd_checked_coordinates": 16, "fd_max_rel_error": worst,
-            "fd_error_scale": "|g_k| + 1e-3 max|g|",
-            "fd_s_per_coordinate": (t4 - t3) / 16,
-            "fd_coordinates_in_adjoint_time": (t2 - t0) / ((t4 - t3) / 16)}
+            "fd_h1e-6": {"coordinates": len(rel_cfg), "max_rel_error": max(rels),
+                         "median_rel_error": float(np.median(rels)),
+                         "per_coordinate": [{"of": r[0], "index": r[1], "grad": r[2], "fd": r[3], "rel_error": r[4]}
+                                            for r in rel_cfg],
+                         "method": "central differences, h = 1e-6; each perturbed solution is x* + d with d "
+                                   "solved to rtol 1e-10 of its own right-hand side b' - A' x*; L(+) - L(-) "
+                                   "evaluated as (x* - x_t).(d+ - d-) + (|d+|^2 - |d-|^2)/2",
+                         "s_per_coordinate": (t4 - t3) / len(rel_cfg)},
+            "fd_large_steps": {"coordinates": 16, "max_rel_error": worst, "error_scale": "|g_k| + 1e-3 max|g|",
+                               "method": "cold starts; b: h = 1e-2; values: Richardson over 5e-3 and 1e-2"}}
 
 
 def run_ours(args):

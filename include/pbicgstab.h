@@ -101,6 +101,22 @@ typedef struct {
                                  operations (default 0) */
     int32_t grid;             /* 0 = automatic; > 0 forces the number of thread blocks
                                  (clamped to what can be co-resident) (default 0) */
+    double *d_inner_history;  /* pbicgstab_solve_mixed only: NULL, or device buffer of
+                                 (fixed_iters>0 ? fixed_iters : inner_maxit)+1 doubles that
+                                 receives ||r_i||_2 of the recursive residual of the FIRST
+                                 refinement step's inner solve, i = 0..its iterations (entry 0
+                                 is the norm of the FP32 right-hand side) (default NULL) */
+    int32_t cluster;          /* pbicgstab_solve / bicgstab_solve on an unpreconditioned handle:
+                                 0 = automatic (systems of up to 24576 stored entries -- stencil:
+                                 points x unknowns -- are solved by one thread-block cluster,
+                                 larger ones by a cooperative grid); -1 = always the
+                                 cooperative grid; 2, 4, 8 or 16 = one cluster of that many CTAs
+                                 (default 0; ignored when grid > 0) */
+    int32_t stall_steps;      /* pbicgstab_solve_mixed only: stop (PBCG_NOT_CONVERGED) after this
+                                 many refinement steps in a row that fail to bring the FP64
+                                 residual below the best one so far; 0 = the default, 6 (converging
+                                 refinements with capped inner solves were measured to have up
+                                 to 4 such steps in a row) */
 } pbcg_opts;
 
 /* Result summary, written to host memory by every solve. */
@@ -117,7 +133,8 @@ typedef struct {
     int32_t grid_syncs;       /* device-wide synchronisations performed */
     int32_t spmvs;            /* sparse matrix-vector products performed */
     float kernel_ms;          /* duration of the solver kernel, CUDA events on the handle's stream */
-    int32_t pad;
+    int32_t cluster;          /* > 0: the solve ran on one thread-block cluster of this many CTAs
+                                 (grid == cluster); 0: on a cooperative grid */
 } pbcg_info;
 
 /* Bytes of device workspace a handle for n unknowns needs (256-byte aligned
@@ -200,7 +217,8 @@ typedef struct {
     int32_t grid_syncs;       /* device-wide synchronisations performed */
     int32_t spmvs;            /* sparse matrix-vector products (FP64 and low precision) */
     float kernel_ms;          /* duration of the solve kernel, CUDA events on the handle's stream */
-    int32_t pad;
+    int32_t restored;         /* 1 if the solve stopped unconverged and x was reset to the best
+                                 iterate (the one with the smallest FP64 residual) */
 } pbcg_mixed_info;
 
 /* Low-precision value types for pbicgstab_solve_mixed. */
@@ -212,22 +230,30 @@ enum { PBCG_VALUES_F32 = 0, PBCG_VALUES_BF16 = 1 };
  * handle's FP64 operator, solves A d = r with the FP32 pipelined iteration
  * to ||r_inner|| <= inner_rtol ||r|| (at most inner_maxit iterations) on a
  * low-precision copy of A, and sets x := x + d in FP64. Dot products that set
- * alpha, beta and omega are summed per thread in FP32 (compensated, to FP64
- * accuracy, for CSR handles; a plain FMA chain over the thread's few dozen
- * rows for stencil handles) and across threads in FP64; the scalars are FP64.
- * Stops when the FP64 residual satisfies
- * ||b - A x|| <= rtol ||b - A x0|| or after max_outer steps
- * (PBCG_NOT_CONVERGED).
+ * alpha, beta and omega are summed per thread in compensated FP32 (algorithm
+ * Dot2: as accurate as twice FP32 precision) and across threads in FP64; the
+ * scalars are FP64.
+ * Stops when the FP64 residual satisfies ||b - A x|| <= rtol ||b - A x0||
+ * (PBCG_OK); after max_outer steps (PBCG_NOT_CONVERGED); or when
+ * opts->stall_steps (default 6) steps in a row fail to bring the FP64
+ * residual below the best one so far -- refinement does not contract, e.g.
+ * when cond(A) times the rounding of the low-precision values exceeds 1
+ * (PBCG_NOT_CONVERGED). A solve that stops unconverged returns
+ * the best iterate (info->restored = 1 when that is not the last one) and
+ * info->rel_res_true is that iterate's residual.
  *   h            a CSR or stencil handle
  *   d_val_lowp   CSR handle: nnz values of the same CSR structure as float
  *                (PBCG_VALUES_F32) or bfloat16 (PBCG_VALUES_BF16),
  *                caller-owned. Stencil handle: NULL with PBCG_VALUES_F32; the
  *                library rounds the coefficient tables to FP32 into the
  *                workspace each call (PBCG_ERR_ARG if they need more than the
- *                12 * round32(n) floats the inner vectors leave free, or for
- *                other arguments)
+ *                10 * round32(n) floats the inner vectors and the copy of the
+ *                best iterate leave free, or for other arguments)
  *   opts         NULL or options; d_history (max_outer + 1 doubles) receives
- *                the FP64 residual norm before each step; grid as for solve
+ *                the FP64 residual norm before each step; grid as for solve;
+ *                fixed_iters > 0 makes every inner solve run exactly that many
+ *                iterations (inner_rtol ignored; for step-by-step comparison);
+ *                d_inner_history receives the first inner solve's residual norms
  * Uses the handle's workspace (no extra memory). */
 pbcg_status pbicgstab_solve_mixed(pbicgstab_t h, const void *d_val_lowp, int32_t lowp_type, const double *d_b,
                                   double *d_x, double rtol, int32_t max_outer, double inner_rtol,
@@ -335,12 +361,15 @@ pbcg_status pbicgstab_probe_sync_timeout(pbicgstab_t h, int32_t limit_ms, int32_
 
 /* Bounds-checked builds (the library compiled with -DPBCG_CHECK; a debugging
  * aid with no counterpart in the paper): the kernels check every index they
- * form from data or geometry (gathered CSR columns, stencil neighbours, row
- * pointers); an out-of-range one is replaced by 0 so that no access leaves
- * its buffer, and the source line of the first is recorded on the current
- * device. Synchronises the device, returns that line (0: none since the last
- * call) and clears it; -2 if a CUDA call fails. The default build has no
- * checks and returns -1. */
+ * form from data or geometry -- CSR entry positions taken from the row
+ * pointers (against nnz), gathered CSR columns, stencil neighbours and
+ * stencil coefficient-table positions (against the table length reached over
+ * the grid), and the gathered columns of the adjoint transpose and value
+ * gradient; an out-of-range one is replaced by 0 so that no access leaves its
+ * buffer, and the source line of the first is recorded on the current device.
+ * Synchronises the device, returns that line (0: none since the last call) and
+ * clears it; -2 if a CUDA call fails. The default build has no checks and
+ * returns -1. */
 int32_t pbicgstab_check_faults(void);
 
 /* Largest system pbicgstab_solve_csr_noalloc accepts. */
@@ -360,7 +389,9 @@ int32_t pbicgstab_check_faults(void);
  *   PBCG_ERR_ARG.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any
- *   stream capture.
+ *   stream capture. The address is kept for the life of the process: after a
+ *   cudaDeviceReset of that device the kept address is stale, so do not call
+ *   this entry point on that device again.
  *   All calls on a device share the one array, and each call resets the parts
  *   that must start from a known state. Calls whose work overlaps on the GPU
  *   (other streams, other host threads) race on it; serialise them.

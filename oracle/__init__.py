@@ -23,6 +23,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# OpenMP build of the same source, for timing the oracle on all host cores
+# (bench.py's CPU legs); the tests use the single-threaded build above.
+_OMP_LIB_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 
 CONVERGED, NOT_CONVERGED, BREAKDOWN, NONFINITE, ERR_ARG, ERR_OOM = range(6)
 
@@ -34,24 +37,30 @@ class OInfo(ctypes.Structure):
                 ("flops", ctypes.c_double), ("spmvs", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library (gcc, -ffp-contract=off)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, -ffp-contract=off);
+    omp=True: the OpenMP build (-fopenmp) used only to time the oracle."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    path = _OMP_LIB_PATH if omp else _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if omp:
+            cmd.insert(1, "-fopenmp")
+        subprocess.check_call(cmd)
+        os.replace(tmp, path)
+    return path
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def lib(omp: bool = False):
+    """The single-threaded oracle library, or (omp=True) its OpenMP build."""
+    if omp not in _libs:
+        L = ctypes.CDLL(build(omp=omp))
+        _libs[omp] = L
+        _lib = L
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int32)
         i32, f64 = ctypes.c_int32, ctypes.c_double
@@ -65,7 +74,13 @@ def lib():
         pcommon = [i32, ip, ip, dp, dp, dp, dp, f64, i32, i32]
         _lib.o_bicgstab_prec.argtypes = pcommon + [dp, dp, dp, ctypes.POINTER(OInfo)]
         _lib.o_pbicgstab_prec.argtypes = pcommon + [i32, i32, dp, dp, dp, ctypes.POINTER(OInfo)]
-    return _lib
+        _lib.o_num_threads.restype = ctypes.c_int
+    return _libs[omp]
+
+
+def num_threads(omp: bool = False) -> int:
+    """Threads the oracle build runs on (1 for the parity build)."""
+    return int(lib(omp).o_num_threads())
 
 
 def _p(a: Optional[np.ndarray], ctype=ctypes.c_double):
@@ -115,7 +130,7 @@ class Result:
 
 
 def _run(method: str, A, b, x0, rtol, maxit, fixed_iters, trace, replace_period=0,
-         max_replacements=-1, alpha_eq5=False, keep_work=False, rr_placement=0) -> Result:
+         max_replacements=-1, alpha_eq5=False, keep_work=False, rr_placement=0, omp=False) -> Result:
     rowptr, col, val = _csr_args(A)
     n = A.n
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -126,7 +141,7 @@ def _run(method: str, A, b, x0, rtol, maxit, fixed_iters, trace, replace_period=
     trr = np.full((steps + 1, n), np.nan) if trace else None
     work = np.zeros(10 * max(n, 1)) if keep_work else None
     info = OInfo()
-    L = lib()
+    L = lib(omp)
     args = [n, _p(rowptr, ctypes.c_int32), _p(col, ctypes.c_int32), _p(val), _p(b), _p(x),
             float(rtol), int(maxit), int(fixed_iters)]
     if method == "bicgstab":
@@ -200,9 +215,9 @@ def pbicgstab_prec(A, minv, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, tr
                      max_replacements)
 
 
-def bicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False) -> Result:
-    """Algorithm 7 (standard BiCGStab) in plain FP64."""
-    return _run("bicgstab", A, b, x0, rtol, maxit, fixed_iters, trace)
+def bicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False, omp=False) -> Result:
+    """Algorithm 7 (standard BiCGStab) in plain FP64 (omp=True: the OpenMP build)."""
+    return _run("bicgstab", A, b, x0, rtol, maxit, fixed_iters, trace, omp=omp)
 
 
 def cabicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False) -> Result:
@@ -212,9 +227,10 @@ def cabicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False)
 
 def pbicgstab(A, b, x0=None, rtol=1e-8, maxit=1000, fixed_iters=0, trace=False,
               replace_period=0, max_replacements=-1, alpha_eq5=False, keep_work=False,
-              rr_placement=0) -> Result:
+              rr_placement=0, omp=False) -> Result:
     """Algorithm 9 (pipelined BiCGStab) with residual replacement every
     ``replace_period`` iterations (0 = off), in plain FP64. ``rr_placement`` 0 is
-    the default (split) placement, 1 the literal late placement (see oracle.c)."""
+    the default (split) placement, 1 the literal late placement (see oracle.c).
+    omp=True runs the OpenMP build (timing only)."""
     return _run("pbicgstab", A, b, x0, rtol, maxit, fixed_iters, trace, replace_period,
-                max_replacements, alpha_eq5, keep_work, rr_placement)
+                max_replacements, alpha_eq5, keep_work, rr_placement, omp)

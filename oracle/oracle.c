@@ -48,6 +48,23 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* The parity build is single-threaded (no -fopenmp: the pragmas below are
+ * ignored and every loop runs in the order written). A second build with
+ * -fopenmp splits the row loops of the SpMV and the vector updates over
+ * threads and sums dot products per thread, for timing the oracle on all host
+ * cores; only that build's dot products are summed in another order. */
+int o_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 enum { O_CONVERGED = 0, O_NOT_CONVERGED = 1, O_BREAKDOWN = 2, O_NONFINITE = 3, O_ERR_ARG = 4, O_ERR_OOM = 5 };
 
@@ -86,6 +103,7 @@ typedef struct {
 /* y = A x, row i summed over its stored entries in order */
 static void spmv(const o_csr *A, const double *x, double *y, o_count *c)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < A->n; i++) {
         double acc = 0.0;
         for (int32_t e = A->rowptr[i]; e < A->rowptr[i + 1]; e++)
@@ -99,6 +117,7 @@ static void spmv(const o_csr *A, const double *x, double *y, o_count *c)
 static double dot(int32_t n, const double *a, const double *b, o_count *c)
 {
     double acc = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
     for (int32_t i = 0; i < n; i++) acc = acc + a[i] * b[i];
     if (c) c->flops += 2.0 * n;
     return acc;
@@ -107,6 +126,7 @@ static double dot(int32_t n, const double *a, const double *b, o_count *c)
 /* out = x + alpha * z (out may alias x or z) */
 static void axpy(int32_t n, double *out, const double *x, double alpha, const double *z, o_count *c)
 {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < n; i++) out[i] = x[i] + alpha * z[i];
     if (c) c->flops += 2.0 * n;
 }
@@ -124,6 +144,7 @@ static int finite_all(int cnt, const double *v)
 static double true_residual(const o_csr *A, const double *b, const double *x, double *res)
 {
     spmv(A, x, res, NULL);
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < A->n; i++) res[i] = b[i] - res[i];
     return norm2(A->n, res);
 }

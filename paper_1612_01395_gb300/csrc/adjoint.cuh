@@ -51,7 +51,7 @@ __global__ void transpose_scatter_kernel(int n, const int *rowptr, const int *co
                                          const int *trow, int *cursor, int *tcol, double *tval) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
-            const int c = col[k];
+            const int c = PBCG_SAFE(col[k], n);
             const int pos = trow[c] + atomicAdd(&cursor[c], 1);
             tcol[pos] = i;
             tval[pos] = val[k];
@@ -83,7 +83,7 @@ __global__ void value_grad_kernel(int n, const int *rowptr, const int *col, cons
                                   double *g) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double li = lambda[i];
-        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) g[k] = -li * x[col[k]];
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) g[k] = -li * x[PBCG_SAFE(col[k], n)];
     }
 }
 

@@ -309,6 +309,59 @@ __device__ __forceinline__ bool grid_sum(BlockSync &g, double (&v)[K], double (*
 }
 
 // ---------------------------------------------------------------------------
+// 1-D bulk copies from global into shared memory (the TMA unit's untiled
+// copy, cp.async.bulk), completed on a shared-memory mbarrier. One thread
+// posts the expected byte count and issues the copies; every thread waits on
+// the barrier's phase. Addresses and sizes must be multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Make barrier initialisations visible to the asynchronous (copy) proxy.
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Order this thread's earlier generic-proxy global accesses before later
+// bulk copies (async proxy) of the same memory.
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Wait until the barrier's phase of the given parity has completed. Bounded:
+// after kSyncTimeoutNs the launch is flagged PBCG_ERR_TIMEOUT and false is
+// returned (a copy can only stay incomplete if its byte count disagreed with
+// the posted one).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, Control *ctl) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer_ns() - t0 > kSyncTimeoutNs) {
+            atomicCAS(&ctl->abort, 0, (int)PBCG_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Thread-block clusters (batched solves of large systems). The CTAs of a
 // cluster are co-scheduled by the hardware, so a wait on the hardware cluster
 // barrier always completes once every CTA reaches it; each CTA can address
@@ -353,16 +406,19 @@ __device__ __forceinline__ void st_cluster_s32(uint32_t addr, int v) {
 }
 
 // Synchronisation policy of a solve shared by the `size` CTAs of a cluster:
-// a barrier is the cluster barrier; a reduction publishes each CTA's block
-// sums into its slot in the shared memory of CTA 0 (two alternating buffers),
-// crosses the barrier, and every CTA adds the slots in rank order -- the same
-// additions in the same order everywhere, so all CTAs hold identical scalars.
-// A slot buffer is rewritten two reductions later, after the barrier of the
-// reduction in between, which every CTA reaches only when it has finished
-// reading. Same interface as GridSync and BlockSync.
+// a barrier is the cluster barrier; a reduction pushes each CTA's K block sums
+// into slot [rank] of EVERY CTA's slot array (distributed shared memory,
+// posted stores), crosses the barrier, and then each warp of each CTA adds the
+// `size` slots of its own shared memory with the same fixed-order warp
+// reduction -- the same additions in the same order everywhere, so all CTAs
+// (and all warps) hold identical scalars, with no remote loads on the
+// critical path and no block barrier after the sum. Slot arrays alternate
+// between two buffers: buffer e % 2 is rewritten by exchange e + 2, which a
+// CTA starts only after the barrier of exchange e + 1, which every thread of
+// every CTA reaches only after it has read exchange e. Same interface as
+// GridSync and BlockSync.
 struct ClusterSync {
-    uint32_t slots0;    // cluster address of CTA 0's slot array [2][kMaxCluster][kSlotDoubles]
-    double *bcast;      // this CTA's shared [kMaxDots]: the cluster sums, for every thread
+    double (*slots)[kMaxCluster][kSlotDoubles];   // this CTA's shared [2][kMaxCluster][kSlotDoubles]
     unsigned rank, size;
     unsigned epoch;     // reductions done
     int count;
@@ -377,22 +433,22 @@ __device__ __forceinline__ bool grid_sync(ClusterSync &g, double (*)[32], int *)
 template <int K>
 __device__ __forceinline__ bool grid_sum(ClusterSync &g, double (&v)[K], double (*sm)[32], int *) {
     block_sum<K>(v, sm);   // ends with __syncthreads; every thread holds the block sums
-    const uint32_t buf = g.slots0 + (g.epoch & 1u) * (uint32_t)(kMaxCluster * kSlotDoubles * sizeof(double));
-    if (threadIdx.x == 0) {
+    const unsigned buf = g.epoch & 1u;
+    const unsigned t = threadIdx.x;
+    if (t < g.size * K) {
+        const unsigned dst = t / K, k = t - dst * K;
+        double mine = v[0];
 #pragma unroll
-        for (int k = 0; k < K; ++k) st_cluster_f64(buf + (g.rank * kSlotDoubles + k) * sizeof(double), v[k]);
+        for (int q = 1; q < K; ++q)
+            if ((int)k == q) mine = v[q];
+        st_cluster_f64(cluster_map(&g.slots[buf][g.rank][k], dst), mine);
     }
     cluster_barrier();
-    if (threadIdx.x < K) {
-        double t = 0.0;
-        for (unsigned r = 0; r < g.size; ++r)
-            t += ld_cluster_f64(buf + (r * kSlotDoubles + threadIdx.x) * sizeof(double));
-        g.bcast[threadIdx.x] = t;
-    }
-    __syncthreads();
+    // every warp: lane l holds slot l, then a fixed-order warp sum
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = g.bcast[k];
-    __syncthreads();
+    for (int k = 0; k < K; ++k) v[k] = lane < (int)g.size ? g.slots[buf][lane][k] : 0.0;
+    warp_allsum<K>(v);
     g.epoch++;
     g.count++;
     return true;

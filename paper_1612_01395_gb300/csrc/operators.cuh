@@ -76,6 +76,7 @@ struct CsrOpT {
     const int *__restrict__ rowptr;
     const int *__restrict__ col;
     const V *__restrict__ val;
+    int nnz;   // entries readable at col and val (the bounds of a checked build)
 
     template <class L>
     __device__ __forceinline__ auto row(int r, const L &u) const -> decltype(u(0)) {
@@ -83,7 +84,10 @@ struct CsrOpT {
         const int b = __ldg(rowptr + PBCG_SAFE(r, n)), e = __ldg(rowptr + PBCG_SAFE(r, n) + 1);
         T acc = T(0);
         if constexpr (kChunk <= 1) {
-            for (int k = b; k < e; ++k) acc = fmaT(value_as<T>(__ldg(val + k)), u(PBCG_SAFE(__ldg(col + k), n)), acc);
+            for (int k = b; k < e; ++k) {
+                const int kk = PBCG_SAFE(k, nnz);
+                acc = fmaT(value_as<T>(__ldg(val + kk)), u(PBCG_SAFE(__ldg(col + kk), n)), acc);
+            }
         } else {
             for (int k0 = b; k0 < e; k0 += kChunk) {
                 int c[kChunk] = {};
@@ -92,8 +96,9 @@ struct CsrOpT {
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
                     if (k0 + j < e) {
-                        c[j] = __ldg(col + k0 + j);
-                        v[j] = __ldg(val + k0 + j);
+                        const int kk = PBCG_SAFE(k0 + j, nnz);
+                        c[j] = __ldg(col + kk);
+                        v[j] = __ldg(val + kk);
                     }
 #pragma unroll
                 for (int j = 0; j < kChunk; ++j)
@@ -121,6 +126,7 @@ struct StCoefT {
     int a1, b1, c1, a2, b2, c2;
     int n2;
     C value;
+    int len1, len2;   // elements readable at t1 and t2 (the bounds of a checked build)
 };
 using StCoef = StCoefT<double>;
 
@@ -136,7 +142,7 @@ struct StencilOpT {
 
     __device__ __forceinline__ C coef(int d, int i, int j, int k) const {
         const StCoefT<C> &q = c[d];
-        C v = q.t1 ? __ldg(q.t1 + (i * q.a1 + j * q.b1 + k * q.c1)) : q.value;
+        C v = q.t1 ? __ldg(q.t1 + PBCG_SAFE(i * q.a1 + j * q.b1 + k * q.c1, q.len1)) : q.value;
         // The second table is rare (a coefficient varying along two separate
         // directions), and its addition is written as a loop of n2 (0 or 1)
         // trips so that the compiler jumps over it rather than predicating it:
@@ -145,7 +151,7 @@ struct StencilOpT {
         // this GPU), which as an if-converted branch cost 6 dead DADDs per row
         // of a 7-point stencil with one summed coefficient.
 #pragma unroll 1
-        for (int m = 0; m < q.n2; ++m) v = add_rn(v, __ldg(q.t2 + (i * q.a2 + j * q.b2 + k * q.c2)));
+        for (int m = 0; m < q.n2; ++m) v = add_rn(v, __ldg(q.t2 + PBCG_SAFE(i * q.a2 + j * q.b2 + k * q.c2, q.len2)));
         return v;
     }
 
@@ -174,16 +180,16 @@ struct StencilOpT {
         const StCoefT<C> &q = c[d];
         if (q.t1) {
             const int at = i * q.a1 + j * q.b1 + k * q.c1;
-            v0 = __ldg(q.t1 + at);
-            v1 = q.a1 == 0 ? v0 : __ldg(q.t1 + at + q.a1);
+            v0 = __ldg(q.t1 + PBCG_SAFE(at, q.len1));
+            v1 = q.a1 == 0 ? v0 : __ldg(q.t1 + PBCG_SAFE(at + q.a1, q.len1));
         } else {
             v0 = v1 = q.value;
         }
 #pragma unroll 1
         for (int m = 0; m < q.n2; ++m) {
             const int at = i * q.a2 + j * q.b2 + k * q.c2;
-            const C w0 = __ldg(q.t2 + at);
-            const C w1 = q.a2 == 0 ? w0 : __ldg(q.t2 + at + q.a2);
+            const C w0 = __ldg(q.t2 + PBCG_SAFE(at, q.len2));
+            const C w1 = q.a2 == 0 ? w0 : __ldg(q.t2 + PBCG_SAFE(at + q.a2, q.len2));
             v0 = add_rn(v0, w0);
             v1 = add_rn(v1, w1);
         }

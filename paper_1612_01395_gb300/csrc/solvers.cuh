@@ -108,8 +108,8 @@ __device__ __forceinline__ double beta_of(double alpha, double omega, double rho
 
 // Final true residual ||b - A x|| and the result record (block 0). The
 // history holds squared norms during the loop; they become norms here.
-template <class Op>
-__device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32], int *sflag,
+template <class Op, class Sync>
+__device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, Sync &g, double (*sm)[32], int *sflag,
                                        int lo, int hi, const Outcome &o, int spmvs) {
     double d[1] = {0.0};
     PBCG_ROWS(i) {
@@ -139,17 +139,18 @@ __device__ __forceinline__ void finish(const Op &A, const SolveArgs &a, GridSync
 
 // Per-thread accumulation of a dot product over the rows of a sweep. FP64
 // vectors: an FMA into a double. FP32 vectors (the inner solves of the
-// mixed-precision refinement; CSR form, see DotAccFma for the stencil form):
-// compensated FP32 accumulation, algorithm Dot2
-// of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
-// Comput. 26, 2005): each product is split exactly into its rounded value and
-// rounding error (TwoProduct by FMA), the running sum is updated by the
-// error-free TwoSum and all errors are summed apart; the result is as accurate
-// as if accumulated in twice the working precision and is converted to double
-// once per thread and sweep. On this GPU an FP32 operation costs 1/64 of an
-// FP64 one, so the inner solves keep FP64-grade dot products without any FP64
-// instruction per row. Explicit _rn intrinsics keep the compiler from fusing
-// the steps of the error-free transformations.
+// mixed-precision refinement, CSR and stencil form): compensated FP32
+// accumulation, algorithm Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005): each product is split exactly into
+// its rounded value and rounding error (TwoProduct by FMA), the running sum is
+// updated by the error-free TwoSum and all errors are summed apart; the result
+// is as accurate as if accumulated in twice the working precision and is
+// converted to double once per thread and sweep, and the threads' values are
+// summed in FP64. On this GPU an FP32 operation costs 1/64 of an FP64 one, so
+// the inner solves keep FP64-grade dot products (the ones that set alpha,
+// beta and omega) without any FP64 instruction per row. Explicit _rn
+// intrinsics keep the compiler from fusing the steps of the error-free
+// transformations.
 template <typename T>
 struct DotAcc;
 template <>
@@ -172,24 +173,9 @@ struct DotAcc<float> {
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
-// Plain FP32 accumulation by FMA, converted to double once per thread and
-// sweep (a thread sums a few dozen rows; the block and grid sums are FP64).
-// The stencil-form inner sweeps use it: their instruction count shows in their
-// time, and Dot2's eight operations per product cost 10 % per inner iteration
-// (192^3: 279 against 251 us); the CSR form, bound by its matrix traffic,
-// measured the same either way and keeps Dot2.
-struct DotAccFma {
-    float s = 0.0f;
-    __device__ __forceinline__ void add(float a, float b) { s = __fmaf_rn(a, b, s); }
-    __device__ __forceinline__ double value() const { return (double)s; }
-};
 template <class Op, typename T>
 struct DotAccFor {
     using type = DotAcc<T>;
-};
-template <>
-struct DotAccFor<StencilOpT<float>, float> {
-    using type = DotAccFma;
 };
 
 template <class Acc, int K>
@@ -228,6 +214,77 @@ __device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[
 }
 
 // ===========================================================================
+// Staged FP32 stencil sweeps (the inner solves of the mixed-precision
+// refinement). These sweeps move 96 bytes per unknown and iteration and were
+// bound by load latency with every thread issuing its own vector loads. Here
+// the vectors a phase streams (read once, by the rows' own block) arrive in
+// shared memory by 1-D bulk copies: a block walks its rows in tiles of
+// kStageRows, thread 0 keeps kStages - 1 tiles in flight ahead of the one being
+// computed (one mbarrier per buffer), and the threads read their rows from
+// shared memory. The SpMV input (neighbours in other tiles and blocks) and the
+// stores stay ordinary global accesses. Block row ranges start on multiples
+// of 4 rows, so every copy starts on a 16-byte boundary; the last tile's copy
+// is rounded up to 16 bytes, inside the vectors' padding.
+// ===========================================================================
+constexpr int kStageRows = 2 * kTPB;   // rows per tile: one pair per thread
+constexpr int kStages = 3;             // buffers: 2 tiles in flight ahead
+constexpr int kStageVecs = 6;          // streamed vectors per phase
+constexpr size_t kStageSmemBytes = (size_t)kStages * kStageVecs * kStageRows * sizeof(float);
+
+struct Stager {
+    float *buf;      // shared [kStages][kStageVecs][kStageRows]
+    uint64_t *bar;   // shared [kStages]
+    unsigned seq;    // tiles begun by this block so far (every thread holds the same value)
+    Control *ctl;
+};
+
+// thread 0: post and issue the copies of tile `seq` (rows [row0, row0 + rows)).
+__device__ __forceinline__ void stage_issue(const Stager &S, unsigned seq, const float *const *src, int row0, int rows) {
+    const unsigned b = seq % kStages;
+    const unsigned bytes = (unsigned)((rows + 3) & ~3) * (unsigned)sizeof(float);
+    mbar_arrive_expect_tx(&S.bar[b], bytes * kStageVecs);
+#pragma unroll
+    for (int k = 0; k < kStageVecs; ++k)
+        bulk_g2s(S.buf + ((size_t)b * kStageVecs + k) * kStageRows, src[k] + row0, bytes, &S.bar[b]);
+}
+
+// Run body(tile buffer, first row of the tile) over the block's rows [lo, hi)
+// with the six vectors `src` staged. Returns false if a wait timed out.
+template <class Body>
+__device__ __forceinline__ bool staged_sweep(Stager &S, const float *const *src, int lo, int hi, Body body) {
+    const int ntiles = hi > lo ? (hi - lo + kStageRows - 1) / kStageRows : 0;
+    // every thread: earlier generic writes of these rows (this block's, made
+    // visible by the preceding barriers) before the copies read them
+    fence_proxy_async_global();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 0; t < kStages - 1 && t < ntiles; ++t) {
+            const int r0 = lo + t * kStageRows;
+            stage_issue(S, S.seq + t, src, r0, hi - r0 < kStageRows ? hi - r0 : kStageRows);
+        }
+    for (int t = 0; t < ntiles; ++t) {
+        const unsigned seq = S.seq + (unsigned)t;
+        const int ahead = t + kStages - 1;
+        if (threadIdx.x == 0 && ahead < ntiles) {   // its buffer was released by the barrier ending tile t - 1
+            const int r0 = lo + ahead * kStageRows;
+            stage_issue(S, seq + kStages - 1, src, r0, hi - r0 < kStageRows ? hi - r0 : kStageRows);
+        }
+        if (!mbar_wait(&S.bar[seq % kStages], (seq / kStages) & 1u, S.ctl)) return false;
+        body(S.buf + (size_t)(seq % kStages) * kStageVecs * kStageRows, lo + t * kStageRows);
+        __syncthreads();   // every thread is done with this buffer before it is refilled
+    }
+    S.seq += (unsigned)ntiles;
+    return true;
+}
+
+// Elements j, j+1 of a staged vector (j even: one 64-bit shared load).
+__device__ __forceinline__ void staged_pair(const float *tb, int k, int j, float (&out)[2]) {
+    const float2 v = *reinterpret_cast<const float2 *>(tb + k * kStageRows + j);
+    out[0] = v.x;
+    out[1] = v.y;
+}
+
+// ===========================================================================
 // Algorithm 9 (pipelined BiCGStab) with the residual replacement of
 // Section 4.2 (r := b - A x, w := A r before the second reduction of iteration
 // i-1; s := A p, z := A s after p_i; for i mod k == 0).
@@ -238,7 +295,8 @@ __device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[
 // alpha, beta, omega, rho are doubles; a sweep uses them rounded to T.
 template <class Op, typename T, class Sync = GridSync>
 __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> &a, Sync &g, double (*sm)[32],
-                                               int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
+                                               int *sflag, int lo, int hi, Outcome &o, int &spmvs,
+                                               Stager *stg = nullptr) {
     const VectorsT<T> &V = a.V;
     T *x = a.x;
     const bool fixed = a.fixed != 0;
@@ -299,7 +357,61 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         // ---- phase A: t_i = A w_i; p_i, s_i, z_i, q_i, y_i; first reduction
         Acc a1[5];   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         const T al = (T)alpha, be = (T)beta, om = (T)omega;
-        if (!replaced_rw) {
+        bool swept = false;   // the staged sweep did phase A
+        if constexpr (kGroup == 2 && HasRow2<Op>::value) {
+            if (!replaced_rw && stg) {
+                // staged: r s z p v r0 through shared memory, w (SpMV) from global
+                const float *src[kStageVecs] = {V.r, V.s, V.z, V.p, V.v, V.r0};
+                const bool ok = staged_sweep(*stg, src, lo, hi, [&](const float *tb, int row0) {
+                    const int j = 2 * (int)threadIdx.x;
+                    const int i0 = row0 + j;
+                    if (i0 >= hi) return;
+                    const int cnt = hi - i0 < 2 ? hi - i0 : 2;
+                    T ti[2] = {}, ri[2], wi[2], si[2], zi[2], pi[2], vi[2], r0i[2];
+                    if (cnt == 2 && A.pairs_on_lines()) {
+                        A.row2(i0, V.w, ti);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+                            if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
+                    }
+                    load_group(V.w, i0, cnt, wi);
+                    staged_pair(tb, 0, j, ri);
+                    staged_pair(tb, 1, j, si);
+                    staged_pair(tb, 2, j, zi);
+                    staged_pair(tb, 3, j, pi);
+                    staged_pair(tb, 4, j, vi);
+                    staged_pair(tb, 5, j, r0i);
+                    T pn[2], sn[2], zn[2], qn[2], yn[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        pn[u] = fmaT(be, fmaT(-om, si[u], pi[u]), ri[u]);   // p_i
+                        sn[u] = fmaT(be, fmaT(-om, zi[u], si[u]), wi[u]);   // s_i, eq. (1)
+                        zn[u] = fmaT(be, fmaT(-om, vi[u], zi[u]), ti[u]);   // z_i, eq. (6)
+                        qn[u] = fmaT(-al, sn[u], ri[u]);                    // q_i
+                        yn[u] = fmaT(-al, zn[u], wi[u]);                    // y_i, eq. (4)
+                        if (u < cnt) {
+                            a1[0].add(qn[u], yn[u]);
+                            a1[1].add(yn[u], yn[u]);
+                            a1[2].add(qn[u], qn[u]);
+                            a1[3].add(r0i[u], sn[u]);
+                            a1[4].add(r0i[u], zn[u]);
+                        }
+                    }
+                    store_group(V.t, i0, cnt, ti);
+                    store_group(V.p, i0, cnt, pn);
+                    store_group(V.s, i0, cnt, sn);
+                    store_group(V.z, i0, cnt, zn);
+                    store_group(V.q, i0, cnt, qn);
+                    store_group(V.y, i0, cnt, yn);
+                });
+                if (!ok) return false;
+                ++spmvs;
+                swept = true;
+            }
+        }
+        if (swept) {
+        } else if (!replaced_rw) {
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
                 const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
                 T ti[kGroup] = {}, ri[kGroup], wi[kGroup], si[kGroup], zi[kGroup], pi[kGroup], vi[kGroup], r0i[kGroup];
@@ -398,7 +510,54 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                                  (a.max_repl < 0 || o.nrr < a.max_repl);
         Acc a2[3];   // (r0,r) (r0,w) (r,r)
         const T om2 = (T)omega;
-        if (!replace_now) {
+        bool swept_b = false;   // the staged sweep did phase B
+        if constexpr (kGroup == 2 && HasRow2<Op>::value) {
+            if (!replace_now && stg) {
+                // staged: q y x p t r0 through shared memory, z (SpMV) from global
+                const float *src[kStageVecs] = {V.q, V.y, x, V.p, V.t, V.r0};
+                const bool ok = staged_sweep(*stg, src, lo, hi, [&](const float *tb, int row0) {
+                    const int j = 2 * (int)threadIdx.x;
+                    const int i0 = row0 + j;
+                    if (i0 >= hi) return;
+                    const int cnt = hi - i0 < 2 ? hi - i0 : 2;
+                    T vi[2] = {}, qi[2], yi[2], xi[2], pi[2], ti[2], r0i[2];
+                    if (cnt == 2 && A.pairs_on_lines()) {
+                        A.row2(i0, V.z, vi);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+                            if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
+                    }
+                    staged_pair(tb, 0, j, qi);
+                    staged_pair(tb, 1, j, yi);
+                    staged_pair(tb, 2, j, xi);
+                    staged_pair(tb, 3, j, pi);
+                    staged_pair(tb, 4, j, ti);
+                    staged_pair(tb, 5, j, r0i);
+                    T xn[2], rn[2], wn[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        xn[u] = fmaT(om2, qi[u], fmaT(al, pi[u], xi[u]));
+                        rn[u] = fmaT(-om2, yi[u], qi[u]);                     // eq. (7)
+                        wn[u] = fmaT(-om2, fmaT(-al, vi[u], ti[u]), yi[u]);   // eq. (8)
+                        if (u < cnt) {
+                            a2[0].add(r0i[u], rn[u]);
+                            a2[1].add(r0i[u], wn[u]);
+                            a2[2].add(rn[u], rn[u]);
+                        }
+                    }
+                    store_group(x, i0, cnt, xn);
+                    store_group(V.v, i0, cnt, vi);
+                    store_group(V.r, i0, cnt, rn);
+                    store_group(V.w, i0, cnt, wn);
+                });
+                if (!ok) return false;
+                ++spmvs;
+                swept_b = true;
+            }
+        }
+        if (swept_b) {
+        } else if (!replace_now) {
             for (int i0 = lo + kGroup * (int)threadIdx.x; i0 < hi; i0 += kGroup * kTPB) {
                 const int cnt = kGroup == 1 ? 1 : (hi - i0 < kGroup ? hi - i0 : kGroup);
                 T vi[kGroup] = {}, qi[kGroup], yi[kGroup], xi[kGroup], pi[kGroup], ti[kGroup], r0i[kGroup];
@@ -707,8 +866,8 @@ __global__ void __launch_bounds__(kTPB, Tune<Op>::kMinBlocks) pbicgstab_kernel(c
 // the phase that forms p_i for its SpMV reads p_{i-1}, s_{i-1} of neighbours
 // while writing p_i, s_i, so the old and new values must not share storage.
 // ===========================================================================
-template <class Op>
-__device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
+template <class Op, class Sync = GridSync>
+__device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, Sync &g, double (*sm)[32],
                                               int *sflag, int lo, int hi, Outcome &o, int &spmvs) {
     const Vectors &V = a.V;
     double *x = a.x;
@@ -975,25 +1134,44 @@ __global__ void __launch_bounds__(kTPB, TunePlain<Op>::kMinBlocks) bicgstab_kern
 // Each refinement step computes the true residual r = b - A x with the FP64
 // matrix and FP64 vectors, rounds it to float, solves A d = r with Algorithm 9
 // on float vectors and the low-precision copy of A (FP32 or BF16 values; dot
-// products summed per thread in FP32 and across threads in FP64), and adds d
-// to x in FP64. The true residual of
-// the last step is the reported one. The inner solve runs without residual
-// replacement: the FP64 residual of every refinement step plays that role.
+// products summed per thread in compensated FP32 and across threads in FP64),
+// and adds d to x in FP64. The inner solve runs without residual replacement:
+// the FP64 residual of every refinement step plays that role.
+//
+// Refinement contracts only while the low-precision operator is close enough
+// to A (roughly cond(A) times the value rounding below 1). So the loop also
+// stops when `stall_steps` steps in a row fail to bring the FP64 residual
+// below the best one so far, and returns the best iterate with
+// PBCG_NOT_CONVERGED. A converging refinement can have an occasional step
+// without progress: an inner solve capped at inner_maxit may end on one of
+// BiCGStab's residual peaks. The best iterate is kept without an extra sweep: the
+// sweep that adds d to x first saves x in `xbest` when x is the best so far,
+// i.e. exactly when the loop is about to move away from it.
 // ===========================================================================
+// Default of stall_steps. Measured on the 192^3 convection-diffusion system
+// (40 FP32 refinements to 1e-10: both forms, inner tolerance and cap 0.1/50
+// and 0.03/150, five grids, two roundings of b): runs of up to 4 steps
+// without a new best occur in converging refinements, so 6.
+constexpr int kMixedStallSteps = 6;
+
 struct MixedArgs {
     int n;
     const double *b;
     double *x;
+    double *xbest;       // FP64 copy of the best iterate, written when the loop leaves it
     float *d;            // correction of the current step (inner solution)
     float *rhs;          // residual of the current step, rounded to float
     VectorsT<float> V;   // inner work vectors
     Control *ctl;
     double *partials;
     double *hist;        // nullable: true residual norm before each step, length max_outer + 1
+    double *inner_hist;  // nullable: recursive residual norms of the first step's inner solve
     double rtol;
     int max_outer;
     double inner_rtol;
     int inner_maxit;
+    int inner_fixed;     // > 0: every inner solve runs exactly this many iterations
+    int stall_steps;     // steps in a row without a new best residual that stop the loop
 };
 
 // 9 resident blocks per SM (56 registers). The FP32 inner sweeps are bound by
@@ -1004,18 +1182,38 @@ template <class Op64, class Op32>
 __global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
-    if (threadIdx.x == 0) sflag = 1;   // read only after the first exchange's barrier
+    __shared__ uint64_t stage_bar[kStages];
+    extern __shared__ __align__(128) float stage_buf[];   // kStageSmemBytes when the sweeps are staged
+    constexpr bool kStaged = HasRow2<Op32>::value;
+    if (threadIdx.x == 0) {
+        sflag = 1;   // read only after the first exchange's barrier
+        if (kStaged) {
+            for (int k = 0; k < kStages; ++k) mbar_init(&stage_bar[k], 1);
+            mbar_init_fence();
+        }
+    }
+    __syncthreads();
+    Stager stager{stage_buf, stage_bar, 0u, m.ctl};
     GridSync g{m.ctl, m.partials, 0u, 0};
-    // row ranges start on even rows: the FP32 sweeps access rows in aligned pairs
-    const long long pairs = (m.n + 1) / 2;
-    const int lo = (int)(2 * ((long long)blockIdx.x * pairs / gridDim.x));
-    const int hi_pair = (int)(2 * ((long long)(blockIdx.x + 1) * pairs / gridDim.x));
-    const int hi = hi_pair < m.n ? hi_pair : m.n;
-    int outer = 0, inner_total = 0, status = PBCG_NOT_CONVERGED, spmvs = 0;
+    // row ranges start on multiples of 4 rows: the FP32 sweeps access rows in
+    // aligned pairs, and the staged ones copy 16-byte aligned tiles
+    const long long quads = (m.n + 3) / 4;
+    const int lo = (int)(4 * ((long long)blockIdx.x * quads / gridDim.x));
+    const int hi_quad = (int)(4 * ((long long)(blockIdx.x + 1) * quads / gridDim.x));
+    const int hi = hi_quad < m.n ? hi_quad : m.n;
+    int outer = 0, inner_total = 0, status = PBCG_NOT_CONVERGED, spmvs = 0, stalls = 0;
     double nr0 = 0.0, tol = 0.0, tol2 = 0.0, last = 0.0;
+    double best = 0.0;        // smallest squared FP64 residual so far (valid when have_best)
+    bool have_best = false;
+    bool at_best = false;     // x is the best iterate so far
     for (;;) {
         if (outer > 0) {
-            PBCG_ROWS(i) { m.x[i] = m.x[i] + (double)m.d[i]; }
+            const bool save = at_best;   // the same in every block
+            PBCG_ROWS(i) {
+                const double xi = m.x[i];
+                if (save) m.xbest[i] = xi;
+                m.x[i] = xi + (double)m.d[i];
+            }
             if (!grid_sync(g, sm, &sflag)) return;
         }
         double d[1] = {0.0};
@@ -1034,8 +1232,17 @@ __global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32
             tol2 = __dmul_rn(tol, tol);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0 && m.hist) m.hist[outer] = d[0];
-        if (!isfinite(d[0])) { status = PBCG_NONFINITE; break; }
-        if (nr0 == 0.0 || norm_below(d[0], tol, tol2)) { status = PBCG_OK; break; }
+        if (!isfinite(d[0])) { at_best = false; status = PBCG_NONFINITE; break; }
+        if (nr0 == 0.0 || norm_below(d[0], tol, tol2)) { at_best = true; status = PBCG_OK; break; }
+        if (!have_best || d[0] < best) {
+            best = d[0];
+            have_best = true;
+            at_best = true;
+            stalls = 0;
+        } else {
+            at_best = false;
+            if (++stalls >= m.stall_steps) break;   // refinement does not contract
+        }
         if (outer >= m.max_outer) break;
         SolveArgsT<float> ia;
         ia.n = m.n;
@@ -1044,18 +1251,28 @@ __global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32
         ia.V = m.V;
         ia.ctl = m.ctl;
         ia.partials = m.partials;
-        ia.hist = nullptr;
+        ia.hist = outer == 0 ? m.inner_hist : nullptr;
         ia.rtol = m.inner_rtol;
-        ia.limit = m.inner_maxit;
-        ia.fixed = 0;
+        ia.limit = m.inner_fixed > 0 ? m.inner_fixed : m.inner_maxit;
+        ia.fixed = m.inner_fixed > 0 ? 1 : 0;
         ia.replace_period = 0;
         ia.max_repl = -1;
         ia.variant = 0;
         Outcome io{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
-        if (!pipelined_loop<Op32, float>(A32, ia, g, sm, &sflag, lo, hi, io, spmvs)) return;
+        if (!pipelined_loop<Op32, float>(A32, ia, g, sm, &sflag, lo, hi, io, spmvs, kStaged ? &stager : nullptr))
+            return;
+        // the inner history holds squared norms after entry 0 (thread 0 of block 0 wrote them)
+        if (blockIdx.x == 0 && threadIdx.x == 0 && ia.hist)
+            for (int i = 1; i <= io.iters; ++i) ia.hist[i] = sqrt(ia.hist[i]);
         inner_total += io.iters;
         ++outer;
         if (io.status == PBCG_NONFINITE) { status = PBCG_NONFINITE; break; }
+    }
+    // A solve that stops unconverged returns the best iterate: x := xbest when x is not it.
+    const bool restore = status != PBCG_OK && have_best && !at_best;
+    if (restore) {
+        PBCG_ROWS(i) { m.x[i] = m.xbest[i]; }
+        last = best;
     }
     if (blockIdx.x == 0) {
         if (m.hist)
@@ -1070,8 +1287,40 @@ __global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32
             c->nr0 = nr0;
             c->rel_true = nr0 > 0.0 ? sqrt(last) / nr0 : sqrt(last);
             c->rel_rec = c->rel_true;
+            c->half_step = restore ? 1 : 0;   // mixed solves: 1 if x was reset to the best iterate
         }
     }
+}
+
+// ===========================================================================
+// Single small systems on one thread-block cluster. A cooperative grid pays a
+// round trip through L2 and an arrival counter per exchange (several us at a
+// few thousand unknowns); the CTAs of one cluster instead cross the hardware
+// cluster barrier and exchange their block sums through distributed shared
+// memory (ClusterSync). The solver loops are the same code as on the grid.
+// Rows are split into `size` contiguous ranges, one per CTA; CTA rank 0
+// writes the result record. Every CTA takes the same branches (identical
+// scalars), so all of them execute the same sequence of cluster barriers.
+// ===========================================================================
+template <class Op, bool Pipelined>
+__global__ void __launch_bounds__(kTPB, 1) cluster_solve_kernel(const Op A, const SolveArgs a) {
+    __shared__ double sm[kMaxDots][32];
+    __shared__ double slots[2][kMaxCluster][kSlotDoubles];
+    __shared__ int sflag;
+    const unsigned size = cluster_ctas(), rank = cluster_rank();
+    if (threadIdx.x == 0) sflag = 1;
+    cluster_barrier();   // every CTA started before its shared memory is written by the others
+    ClusterSync g{slots, rank, size, 0u, 0};
+    const int lo = (int)((long long)rank * a.n / size);
+    const int hi = (int)((long long)(rank + 1) * a.n / size);
+    Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
+    int spmvs = 0;
+    if constexpr (Pipelined)
+        pipelined_loop<Op, double, ClusterSync>(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    else
+        standard_loop<Op, ClusterSync>(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    finish(A, a, g, sm, &sflag, lo, hi, o, spmvs);
+    cluster_barrier();   // no CTA leaves while another may still address its shared memory
 }
 
 // M^{-1} = 1 / diag(A) (Jacobi). A zero or non-finite diagonal entry sets *bad.
@@ -1144,7 +1393,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
     int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
     const int n = bad ? 0 : (int)(r1 - r0);
     const int lo = (int)((long long)part * n / parts), hi = (int)((long long)(part + 1) * n / parts);
-    const CsrOpScalar A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val};
+    const CsrOpScalar A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val, B.nnz};
     PBCG_ROWS(i) {
         const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
         if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
@@ -1195,8 +1444,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
 
 __global__ void __launch_bounds__(kTPB, 6) batched_kernel(const BatchArgs B) {
     __shared__ double sm[kMaxDots][32];
-    __shared__ double slots[2][kMaxCluster][kSlotDoubles];   // used in CTA 0 of a cluster
-    __shared__ double bcast[kMaxDots];
+    __shared__ double slots[2][kMaxCluster][kSlotDoubles];   // cluster reductions: every CTA's block sums
     __shared__ int item[2];   // system of this CTA (-1: none), whole-cluster flag (-1: no work left)
     __shared__ int sflag;
     const unsigned size = cluster_ctas(), rank = cluster_rank();
@@ -1231,13 +1479,13 @@ __global__ void __launch_bounds__(kTPB, 6) batched_kernel(const BatchArgs B) {
         const int sys = item[0], whole = item[1];
         if (whole < 0) return;   // the same for every CTA of the cluster
         if (whole == 1) {
-            ClusterSync g{cluster_map(&slots[0][0][0], 0), bcast, rank, size, 0u, 0};
+            ClusterSync g{slots, rank, size, 0u, 0};
             batched_system(B, sys, g, rank, size, sm, &sflag);
         } else if (sys >= 0) {
             BlockSync g{0};
             batched_system(B, sys, g, 0u, 1u, sm, &sflag);
         }
-        // every CTA is done with this item (and with CTA 0's slots) before the next claim
+        // every CTA is done with this item (and with the slots) before the next claim
         if (size > 1) cluster_barrier();
         else __syncthreads();
     }

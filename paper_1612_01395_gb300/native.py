@@ -54,7 +54,8 @@ class PbcgStencil(ctypes.Structure):
 
 class PbcgOpts(ctypes.Structure):
     _fields_ = [("max_replacements", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
-                ("d_history", ctypes.c_void_p), ("plain_variant", ctypes.c_int32), ("grid", ctypes.c_int32)]
+                ("d_history", ctypes.c_void_p), ("plain_variant", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("d_inner_history", ctypes.c_void_p), ("cluster", ctypes.c_int32), ("stall_steps", ctypes.c_int32)]
 
 
 class PbcgInfo(ctypes.Structure):
@@ -62,7 +63,7 @@ class PbcgInfo(ctypes.Structure):
                 ("n_replacements", ctypes.c_int32), ("nr0", ctypes.c_double),
                 ("rel_res_recursive", ctypes.c_double), ("rel_res_true", ctypes.c_double),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("grid_syncs", ctypes.c_int32),
-                ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float), ("pad", ctypes.c_int32)]
+                ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float), ("cluster", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +73,7 @@ class PbcgMixedInfo(ctypes.Structure):
     _fields_ = [("outer", ctypes.c_int32), ("inner_iters", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("nr0", ctypes.c_double), ("rel_res_true", ctypes.c_double),
                 ("grid_syncs", ctypes.c_int32), ("spmvs", ctypes.c_int32), ("kernel_ms", ctypes.c_float),
-                ("pad", ctypes.c_int32)]
+                ("restored", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -185,8 +186,10 @@ class PbcgError(RuntimeError):
         self.status = status
 
 
-def _opts(max_replacements=-1, fixed_iters=0, d_history=None, plain_variant=0, grid=0):
-    return PbcgOpts(int(max_replacements), int(fixed_iters), d_history or None, int(plain_variant), int(grid))
+def _opts(max_replacements=-1, fixed_iters=0, d_history=None, plain_variant=0, grid=0, d_inner_history=None,
+          cluster=0, stall_steps=0):
+    return PbcgOpts(int(max_replacements), int(fixed_iters), d_history or None, int(plain_variant), int(grid),
+                    d_inner_history or None, int(cluster), int(stall_steps))
 
 
 # ---- thin wrappers with the C names ---------------------------------------------------------
@@ -488,25 +491,34 @@ class Solver:
         return x, d
 
     def solve_mixed(self, b, values_lowp, lowp_type=PBCG_VALUES_F32, x0=None, rtol=1e-10, max_outer=30,
-                    inner_rtol=1e-4, inner_maxit=2000, history=False, **opts):
+                    inner_rtol=1e-4, inner_maxit=2000, history=False, inner_history=False, **opts):
         """FP64 refinement around FP32 Algorithm 9. CSR handles: values_lowp is a
         float32 or bfloat16 tensor with the CSR values; stencil handles: None
-        (the library rounds the coefficient tables). Returns (x, info[, history])."""
+        (the library rounds the coefficient tables). Returns (x, info[, history]
+        [, inner_history]): the FP64 residual norm before each step, and the
+        recursive residual norms of the first step's inner solve."""
         torch = self._torch()
         x = torch.zeros_like(b) if x0 is None else x0.clone()
-        hist = None
+        hist = ihist = None
         if history:
             hist = torch.full((max_outer + 1,), float("nan"), dtype=torch.float64, device=b.device)
             opts["d_history"] = hist.data_ptr()
+        if inner_history:
+            steps = opts.get("fixed_iters", 0) or inner_maxit
+            ihist = torch.full((steps + 1,), float("nan"), dtype=torch.float64, device=b.device)
+            opts["d_inner_history"] = ihist.data_ptr()
         vp = values_lowp.data_ptr() if values_lowp is not None else None
         st, info = pbicgstab_solve_mixed(self.h, vp, lowp_type, b.data_ptr(), x.data_ptr(),
                                          rtol, max_outer, inner_rtol, inner_maxit, **opts)
         if st in (PBCG_ERR_ARG, PBCG_ERR_CUDA, PBCG_ERR_OOM, PBCG_ERR_TIMEOUT):
             raise PbcgError(st, pbicgstab_last_error())
         d = info.as_dict()
+        out = (x, d)
         if hist is not None:
-            return x, d, hist[: d["outer"] + 1]
-        return x, d
+            out += (hist[: d["outer"] + 1],)
+        if ihist is not None:
+            out += (ihist,)
+        return out
 
     def close(self):
         if self.h:

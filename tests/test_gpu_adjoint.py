@@ -103,3 +103,63 @@ def test_adjoint_gradients_match_central_differences():
     for k in (P.splitmix64(12, 16) % np.uint64(A.nnz)).astype(int):
         fd = (4 * central_v(k, 5e-3) - central_v(k, 1e-2)) / 3
         assert abs(fd - gv[k]) <= 1e-6 * (abs(gv[k]) + sv), k
+
+
+def test_adjoint_gradients_match_oracle_adjoint_at_256():
+    """The GPU adjoint against the oracle's adjoint on the largest grid the
+    oracle solves in test time (256^2 = 65536 unknowns, both solves to 1e-13)."""
+    A, b, xt, st = setup(n=256, seed=3)
+    L, x, gb, gv = gpu_loss_and_grads(A, b, xt, st)
+    xo, gbo, gvo = oracle_gradients(A, b, xt)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-9
+    assert np.linalg.norm(gb - gbo) / np.linalg.norm(gbo) <= 1e-8
+    assert np.linalg.norm(gv - gvo) / np.linalg.norm(gvo) <= 1e-8
+
+
+def test_adjoint_central_differences_with_step_1e6():
+    """The configured check: central differences with h = 1e-6 on 32 random
+    coordinates (16 of b, 16 of the values), per-coordinate relative error, no
+    floor. A perturbed solution is x* + d with A' d = b' - A' x* solved to rtol
+    1e-10 of its own right-hand side (so d's error scales with h), and
+    L(+) - L(-) is evaluated as (x* - x_t).(d+ - d-) + (|d+|^2 - |d-|^2)/2,
+    which is exact algebra for this quadratic loss and avoids cancelling two
+    nearly equal losses. Truncation is O(h^2) ~ 1e-12 relative and the
+    corrections carry ~1e-10 relative error, so 1e-6 per coordinate leaves
+    room only for coordinates whose gradient is far below the terms of the
+    dot product."""
+    import torch
+    from paper_1612_01395_gb300.adjoint import sparse_solve
+    A, b, xt, st = setup()
+    L, x, gb, gv = gpu_loss_and_grads(A, b, xt, st)
+    vals0 = torch.from_numpy(A.val).cuda()
+    b0 = torch.from_numpy(b).cuda()
+    xt_d = torch.from_numpy(xt).cuda()
+    xstar = sparse_solve(vals0, b0, st, rtol=1e-13).detach()
+
+    def correction(v, bvec):
+        s = native.Solver()
+        ws, nb = s._workspace(A.n, None)
+        s.h = native.pbicgstab_create_csr(A.n, A.nnz, st.rowptr.data_ptr(), st.col.data_ptr(), v.data_ptr(),
+                                          native.PBCG_PREC_NONE, ws, nb, torch.cuda.current_stream().cuda_stream)
+        d, info = s.solve(bvec - s.spmv(xstar), rtol=1e-10, maxit=20000, replace_period=50)
+        s.close()
+        assert info["status"] == native.PBCG_OK
+        return d
+
+    def numerator(vp, bp, vm, bm):
+        dp, dm = correction(vp, bp), correction(vm, bm)
+        return float(torch.dot(xstar - xt_d, dp - dm) + 0.5 * (torch.dot(dp, dp) - torch.dot(dm, dm)))
+
+    h = 1e-6
+    errs = []
+    for i in (P.splitmix64(21, 16) % np.uint64(A.n)).astype(int):
+        e = torch.zeros_like(b0)
+        e[i] = h
+        fd = numerator(vals0, b0 + e, vals0, b0 - e) / (2 * h)
+        errs.append(abs(fd - gb[i]) / abs(gb[i]))
+    for k in (P.splitmix64(22, 16) % np.uint64(A.nnz)).astype(int):
+        e = torch.zeros_like(vals0)
+        e[k] = h
+        fd = numerator(vals0 + e, b0, vals0 - e, b0) / (2 * h)
+        errs.append(abs(fd - gv[k]) / abs(gv[k]))
+    assert max(errs) <= 1e-6, errs

@@ -1,8 +1,11 @@
 """The bounds-checked build (-DPBCG_CHECK) on the GPU (needs a GB300).
 
 Every solver path runs under the checked library: stencil and CSR forms (both
-CSR operator forms), both methods, the mixed-precision solve (stencil with even
-and odd nx, CSR) and a small batch. No index may be reported out of range, and
+CSR operator forms), both methods, the Jacobi-preconditioned methods
+(Algorithms 10 and 11), the mixed-precision solve (stencil with even and odd
+nx, CSR with FP32 and BF16 values), the SpMV entry point, the
+allocation-free entry point, the adjoint transpose and value gradient, and a
+small batch. No index may be reported out of range, and
 the results must equal the default build's bit for bit: the checks only guard
 indices, they change no arithmetic.
 """
@@ -45,7 +48,39 @@ def run_all():
             x, _ = s.solve_mixed(b, v32, native.PBCG_VALUES_F32, rtol=1e-10, max_outer=30, inner_rtol=1e-3,
                                  inner_maxit=500)
             out[(name, form, "mixed")] = x.cpu().numpy()
+            if form == "csr":
+                v16 = torch.from_numpy(A.val).cuda().to(torch.bfloat16)
+                x, _ = s.solve_mixed(b, v16, native.PBCG_VALUES_BF16, rtol=1e-10, max_outer=30, inner_rtol=1e-2,
+                                     inner_maxit=150)
+                out[(name, form, "mixed_bf16")] = x.cpu().numpy()
+            out[(name, form, "spmv")] = s.spmv(b).cpu().numpy()
             s.close()
+            s = native.Solver.from_stencil(st, prec=native.PBCG_PREC_JACOBI) if form == "stencil" else \
+                native.Solver.from_csr(A, prec=native.PBCG_PREC_JACOBI)
+            for method in ("pipelined", "standard"):
+                x, _ = s.solve(b, rtol=1e-10, maxit=2000, replace_period=20, method=method)
+                out[(name, form, method + "_jacobi")] = x.cpu().numpy()
+            s.close()
+        # the allocation-free entry point
+        rowptr, col, val = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+        x = torch.zeros_like(b)
+        st_, _ = native.pbicgstab_solve_csr_noalloc(A.n, A.nnz, rowptr.data_ptr(), col.data_ptr(), val.data_ptr(),
+                                                    b.data_ptr(), x.data_ptr(), 1e-10, 2000, 20,
+                                                    torch.cuda.current_stream().cuda_stream)
+        assert st_ == native.PBCG_OK
+        out[(name, "csr", "noalloc")] = x.cpu().numpy()
+        # the adjoint building blocks: A^T and the value gradient
+        from paper_1612_01395_gb300.adjoint import CSRStructure
+        cs = CSRStructure(A.rowptr, A.col)
+        stream = torch.cuda.current_stream().cuda_stream
+        assert native.pbicgstab_csr_transpose(cs.n, cs.nnz, cs.rowptr.data_ptr(), cs.col.data_ptr(), val.data_ptr(),
+                                              cs.trowptr.data_ptr(), cs.tcol.data_ptr(), cs.tval.data_ptr(),
+                                              cs.work.data_ptr(), cs.work_bytes, stream) == native.PBCG_OK
+        out[(name, "csr", "transpose")] = cs.tval.cpu().numpy()
+        g = torch.empty_like(val)
+        assert native.pbicgstab_csr_value_grad(cs.n, cs.rowptr.data_ptr(), cs.col.data_ptr(), b.data_ptr(),
+                                               x.data_ptr(), g.data_ptr(), stream) == native.PBCG_OK
+        out[(name, "csr", "value_grad")] = g.cpu().numpy()
     R = P.random_sparse(3001, seed=5)
     s = native.Solver.from_csr(R)
     b = torch.from_numpy(oracle.spmv(R, P.splitmix64_uniform(1, R.n))).cuda()

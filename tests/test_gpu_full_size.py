@@ -3,9 +3,12 @@
 forms, in the launch configuration the benchmark uses (automatic grid).
 
 The oracle cannot run a whole solve at this size in test time, so the checks
-are: every SpMV row against the oracle; the first 10 iterations step by step;
-and, for complete solves, the true residual of the returned x recomputed by
-the oracle's SpMV.
+are: every SpMV row against the oracle; the first 20 iterations step by step
+(the parity horizon: residual norms within 1e-8 and x within 1e-9 of the
+oracle), without residual replacement and with replacement every 5
+iterations (4 replacements inside the window, so the replacement path is
+compared at full size too); and, for complete solves, the true residual of
+the returned x recomputed by the oracle's SpMV.
 """
 import numpy as np
 import pytest
@@ -49,17 +52,37 @@ def test_full_size_spmv_rows(cd3d_256):
     sc.close()
 
 
+K = 20
+_ORACLE = {}
+
+
+def oracle_window(A, b, rr):
+    """The oracle's first K iterations (cached: about 10 s each at this size)."""
+    if rr not in _ORACLE:
+        _ORACLE[rr] = oracle.pbicgstab(A, b, rtol=0.0, maxit=K, fixed_iters=K, replace_period=rr)
+    return _ORACLE[rr]
+
+
+@pytest.mark.parametrize("rr", [0, 5])
 @pytest.mark.parametrize("form", ["stencil", "csr"])
-def test_full_size_first_iterations(cd3d_256, form):
+def test_full_size_first_iterations(cd3d_256, form, rr):
     st, A, xs, b = cd3d_256
-    k = 10
-    ref = oracle.pbicgstab(A, b, rtol=0.0, maxit=k, fixed_iters=k)
+    ref = oracle_window(A, b, rr)
+    assert ref.n_replacements == (K // rr if rr else 0)
     s = native.Solver.from_stencil(st) if form == "stencil" else native.Solver.from_csr(A)
-    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=k, fixed_iters=k, history=True)
+    x, info, hist = s.solve(dev(b), rtol=0.0, maxit=K, fixed_iters=K, replace_period=rr, history=True)
     assert info["status"] == native.PBCG_OK
+    assert info["n_replacements"] == ref.n_replacements
     h = hist.cpu().numpy()
-    assert np.all(np.abs(h - ref.hist) <= 1e-8 * ref.hist + 1e-13 * ref.nr0)
+    assert h.size == K + 1
     xg = x.cpu().numpy()
+    tol = 1e-8 * ref.hist + 1e-13 * ref.nr0
+    if rr and K % rr == 0:
+        # r_K was replaced by the true residual of x_K: two x_K that differ by
+        # dx have true residuals that differ by up to ||A dx|| (triangle
+        # inequality), computed here with the oracle's SpMV
+        tol[-1] += np.linalg.norm(oracle.spmv(A, xg - ref.x))
+    assert np.all(np.abs(h - ref.hist) <= tol), np.abs(h - ref.hist) / ref.hist
     assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-9
     s.close()
 

@@ -75,3 +75,70 @@ def test_bf16_values_on_a_well_conditioned_system():
     res = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-3, values32=bf16_round(A.val.astype(np.float32)))
     assert res["rel_res_true"] <= 1e-10
     assert res["outer"] <= 10
+
+
+def test_lowp_algorithm9_in_float64_matches_the_c_oracle():
+    """pbicgstab_lowp is generic in the working type. In float64 it is plain
+    Algorithm 9 and must follow the C oracle's Algorithm 9 (itself pinned to
+    exact rational arithmetic) to rounding over 20 iterations. The two sum
+    their dot products in different orders (numpy pairwise, C left to right),
+    and BiCGStab amplifies such differences: on the 64^2 system the C oracle's
+    own Algorithms 7 and 9 differ by 4e-11 at iteration 20 and by < 1e-12
+    through iteration 12. So the bars are 1e-12 through iteration 12 and 1e-9
+    to iteration 20 (the random system converges faster, so its relative
+    residuals amplify sooner: 1e-12 through 6, 1e-9 through 10). A wrong
+    coefficient in any recurrence or in the alpha denominator of eq. (3)
+    moves the history by O(1) within two iterations."""
+    import scipy.sparse as sp
+    for A, k_tight, k_loose in ((cd2d_64()[0], 12, 20), (P.random_sparse(500, seed=3), 6, 10)):
+        b = oracle.spmv(A, P.splitmix64_uniform(1, A.n))
+        A64 = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+        x, its, hist = mixed.pbicgstab_lowp(A64, b.copy(), 0.0, 20, fixed_iters=20)
+        ref = oracle.pbicgstab(A, b, rtol=0.0, maxit=20, fixed_iters=20)
+        assert its == 20 and hist.size == 21
+        rel = np.abs(hist - ref.hist) / ref.hist
+        assert np.all(rel[:k_tight + 1] <= 1e-12), rel
+        assert np.all(rel[:k_loose + 1] <= 1e-9), rel
+        ref10 = oracle.pbicgstab(A, b, rtol=0.0, maxit=k_tight, fixed_iters=k_tight)
+        x10, _, _ = mixed.pbicgstab_lowp(A64, b.copy(), 0.0, k_tight, fixed_iters=k_tight)
+        assert np.linalg.norm(x10 - ref10.x) / np.linalg.norm(ref10.x) <= 1e-12
+
+
+def test_lowp_algorithm9_float32_stays_near_float64_early():
+    """The float32 run is the same algorithm: its first iterations agree with
+    the float64 run to a few FP32 roundings (the two drift apart later, as any
+    two rounding orders of BiCGStab do)."""
+    import scipy.sparse as sp
+    A, xs, b = cd2d_64()
+    A64 = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    A32 = sp.csr_matrix((A.val.astype(np.float32), A.col, A.rowptr), shape=(A.n, A.n))
+    _, _, h64 = mixed.pbicgstab_lowp(A64, b.copy(), 0.0, 5, fixed_iters=5)
+    _, _, h32 = mixed.pbicgstab_lowp(A32, b.astype(np.float32), 0.0, 5, fixed_iters=5)
+    assert np.max(np.abs(h32 - h64) / h64) <= 1e-4
+
+
+def test_refinement_stops_when_it_does_not_contract():
+    """With the low-precision values negated, each inner solve returns about
+    -A^{-1} r, so the FP64 residual doubles every step (r + A A^{-1} r = 2 r).
+    The refinement stops after `stall_limit` steps without progress, with
+    status NOT_CONVERGED, and returns the best iterate: x0 = 0 itself,
+    residual ratio 1."""
+    A, xs, b = cd2d_64()
+    for limit in (2, 6):
+        res = mixed.refine(A, b, rtol=1e-10, inner_rtol=1e-3, values32=-A.val.astype(np.float32), stall_limit=limit)
+        assert res["status"] == oracle.NOT_CONVERGED
+        assert res["outer"] == limit and res["restored"]
+        np.testing.assert_allclose(res["history"] / res["history"][0], 2.0 ** np.arange(limit + 1), rtol=1e-3)
+        assert np.all(res["x"] == 0.0)
+        assert res["rel_res_true"] == 1.0
+
+
+def test_refinement_with_fixed_inner_iterations():
+    """inner_fixed runs every inner solve for exactly that many iterations and
+    records the first one's residual history (entry 0 = ||fl32(b)||)."""
+    A, xs, b = cd2d_64()
+    res = mixed.refine(A, b, rtol=1e-10, max_outer=3, inner_fixed=7)
+    assert res["inner_iters"] == 7 * res["outer"]
+    h = res["inner_history"]
+    assert h.size == 8
+    assert h[0] == pytest.approx(np.linalg.norm(b.astype(np.float32).astype(np.float64)), rel=1e-15)

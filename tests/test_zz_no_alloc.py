@@ -6,7 +6,9 @@ loop, a plug-in that only receives input and output pointers). This entry
 point serves them from a fixed array inside the library. The test calls it
 twice in a row through the C ABI, with different right-hand sides so the
 second call starts from the first call's leftovers, and checks each result
-against the handle-based pbicgstab_solve within the parity tolerance.
+against the handle-based pbicgstab_solve within the parity tolerance. Around
+the second call, with the device idle on both sides, the device's free memory
+must not change: the call allocates nothing.
 This file is named to be collected last.
 """
 import ctypes
@@ -36,10 +38,16 @@ def test_noalloc_solve_matches_handle_solve_twice():
         b = ref.spmv(torch.from_numpy(P.splitmix64_uniform(seed, A.n)).cuda())
         x_ref, info_ref = ref.solve(b, rtol=1e-10, maxit=1000, replace_period=20)
         x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         st, info = native.pbicgstab_solve_csr_noalloc(A.n, A.nnz, rowptr.data_ptr(), col.data_ptr(),
                                                       val.data_ptr(), b.data_ptr(), x.data_ptr(), 1e-10, 1000,
                                                       20, stream)
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
         assert st == native.PBCG_OK, native.pbicgstab_last_error()
+        if seed == 1:   # the first call may load the module; the second must leave free memory unchanged
+            assert free_after == free_before, (free_before, free_after)
         assert info.iters == info_ref["iters"]
         xr = x_ref.cpu().numpy()
         assert np.linalg.norm(x.cpu().numpy() - xr) / np.linalg.norm(xr) <= X_TOL

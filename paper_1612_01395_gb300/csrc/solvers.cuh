@@ -219,59 +219,77 @@ __device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[
 // bound by load latency with every thread issuing its own vector loads. Here
 // the vectors a phase streams (read once, by the rows' own block) arrive in
 // shared memory by 1-D bulk copies: a block walks its rows in tiles of
-// kStageRows, thread 0 keeps kStages - 1 tiles in flight ahead of the one being
-// computed (one mbarrier per buffer), and the threads read their rows from
-// shared memory. The SpMV input (neighbours in other tiles and blocks) and the
-// stores stay ordinary global accesses. Block row ranges start on multiples
-// of 4 rows, so every copy starts on a 16-byte boundary; the last tile's copy
-// is rounded up to 16 bytes, inside the vectors' padding.
+// kStageRows, thread 0 keeps kStages - 1 tiles in flight ahead of the one it
+// computes, and the threads read their rows from shared memory. Each buffer
+// has a "full" mbarrier (the copies' bytes arrived) and an "empty" one (all
+// threads have read it): thread 0 refills a buffer only after every thread
+// released it, so warps are not held together tile by tile and may run up to
+// kStages - 1 tiles apart. The SpMV input (neighbours in other tiles and
+// blocks) and the stores stay ordinary global accesses. Block row ranges
+// start on multiples of 4 rows, so every copy starts on a 16-byte boundary;
+// the last tile's copy is rounded up to 16 bytes, inside the vectors' padding.
 // ===========================================================================
-constexpr int kStageRows = 2 * kTPB;   // rows per tile: one pair per thread
-constexpr int kStages = 3;             // buffers: 2 tiles in flight ahead
-constexpr int kStageVecs = 6;          // streamed vectors per phase
-constexpr size_t kStageSmemBytes = (size_t)kStages * kStageVecs * kStageRows * sizeof(float);
+// (The same staging of the FP64 stencil sweeps of Algorithm 9 gave bitwise
+// identical results but was 2.7 % slower at 256^3, 1178 against 1148 us per
+// iteration: those sweeps are bound by the FP64 pipe, and staging only adds
+// instructions. They keep their direct loads.)
+constexpr int kStageTileBytes = 1024;   // per vector and tile: 256 FP32 rows (a pair per thread) or 128 FP64 rows
+constexpr int kStages = 3;              // buffers: 2 tiles in flight ahead
+constexpr int kStageVecs = 6;           // streamed vectors per phase
+constexpr int kStageRows = kStageTileBytes / (int)sizeof(float);   // FP32 rows per tile
+constexpr size_t kStageSmemBytes = (size_t)kStages * kStageVecs * kStageTileBytes;
 
 struct Stager {
-    float *buf;      // shared [kStages][kStageVecs][kStageRows]
-    uint64_t *bar;   // shared [kStages]
-    unsigned seq;    // tiles begun by this block so far (every thread holds the same value)
+    char *buf;         // shared [kStages][kStageVecs][kStageTileBytes]
+    uint64_t *full;    // shared [kStages]: copies of the buffer's tile arrived (count 1 + bytes)
+    uint64_t *empty;   // shared [kStages]: every thread finished reading the buffer (count kTPB)
+    unsigned seq;      // tiles begun by this block so far (every thread holds the same value)
     Control *ctl;
 };
 
-// thread 0: post and issue the copies of tile `seq` (rows [row0, row0 + rows)).
-__device__ __forceinline__ void stage_issue(const Stager &S, unsigned seq, const float *const *src, int row0, int rows) {
+// thread 0: post and issue the copies of tile `seq` (rows [row0, row0 + rows)),
+// the byte count rounded up to 16.
+template <typename T, int NV>
+__device__ __forceinline__ void stage_issue(const Stager &S, unsigned seq, const T *const *src, int row0, int rows) {
     const unsigned b = seq % kStages;
-    const unsigned bytes = (unsigned)((rows + 3) & ~3) * (unsigned)sizeof(float);
-    mbar_arrive_expect_tx(&S.bar[b], bytes * kStageVecs);
+    const unsigned bytes = ((unsigned)rows * (unsigned)sizeof(T) + 15u) & ~15u;
+    mbar_arrive_expect_tx(&S.full[b], bytes * NV);
 #pragma unroll
-    for (int k = 0; k < kStageVecs; ++k)
-        bulk_g2s(S.buf + ((size_t)b * kStageVecs + k) * kStageRows, src[k] + row0, bytes, &S.bar[b]);
+    for (int k = 0; k < NV; ++k)
+        bulk_g2s(S.buf + ((size_t)b * kStageVecs + k) * kStageTileBytes, src[k] + row0, bytes, &S.full[b]);
 }
 
 // Run body(tile buffer, first row of the tile) over the block's rows [lo, hi)
-// with the six vectors `src` staged. Returns false if a wait timed out.
-template <class Body>
-__device__ __forceinline__ bool staged_sweep(Stager &S, const float *const *src, int lo, int hi, Body body) {
-    const int ntiles = hi > lo ? (hi - lo + kStageRows - 1) / kStageRows : 0;
+// with the NV (<= kStageVecs) vectors `src` staged, in tiles of
+// kStageTileBytes / sizeof(T) rows. Every staged vector must be a workspace
+// vector (16-byte aligned, padded past n). Returns false if a wait timed out.
+template <typename T, int NV, class Body>
+__device__ __forceinline__ bool staged_sweep(Stager &S, const T *const *src, int lo, int hi, Body body) {
+    static_assert(NV <= kStageVecs, "at most kStageVecs staged vectors");
+    constexpr int R = kStageTileBytes / (int)sizeof(T);
+    const int ntiles = hi > lo ? (hi - lo + R - 1) / R : 0;
     // every thread: earlier generic writes of these rows (this block's, made
-    // visible by the preceding barriers) before the copies read them
+    // visible by the preceding barriers) before the copies read them; after
+    // this barrier every thread has also released every buffer
     fence_proxy_async_global();
     __syncthreads();
     if (threadIdx.x == 0)
         for (int t = 0; t < kStages - 1 && t < ntiles; ++t) {
-            const int r0 = lo + t * kStageRows;
-            stage_issue(S, S.seq + t, src, r0, hi - r0 < kStageRows ? hi - r0 : kStageRows);
+            const int r0 = lo + t * R;
+            stage_issue<T, NV>(S, S.seq + t, src, r0, hi - r0 < R ? hi - r0 : R);
         }
     for (int t = 0; t < ntiles; ++t) {
         const unsigned seq = S.seq + (unsigned)t;
         const int ahead = t + kStages - 1;
-        if (threadIdx.x == 0 && ahead < ntiles) {   // its buffer was released by the barrier ending tile t - 1
-            const int r0 = lo + ahead * kStageRows;
-            stage_issue(S, seq + kStages - 1, src, r0, hi - r0 < kStageRows ? hi - r0 : kStageRows);
+        if (threadIdx.x == 0 && ahead < ntiles) {
+            // the buffer of tile seq + kStages - 1 last held tile seq - 1: wait until all threads released it
+            if (seq >= 1 && !mbar_wait(&S.empty[(seq - 1) % kStages], ((seq - 1) / kStages) & 1u, S.ctl)) return false;
+            const int r0 = lo + ahead * R;
+            stage_issue<T, NV>(S, seq + kStages - 1, src, r0, hi - r0 < R ? hi - r0 : R);
         }
-        if (!mbar_wait(&S.bar[seq % kStages], (seq / kStages) & 1u, S.ctl)) return false;
-        body(S.buf + (size_t)(seq % kStages) * kStageVecs * kStageRows, lo + t * kStageRows);
-        __syncthreads();   // every thread is done with this buffer before it is refilled
+        if (!mbar_wait(&S.full[seq % kStages], (seq / kStages) & 1u, S.ctl)) return false;
+        body(reinterpret_cast<const T *>(S.buf + (size_t)(seq % kStages) * kStageVecs * kStageTileBytes), lo + t * R);
+        mbar_arrive(&S.empty[seq % kStages]);   // this thread is done with the buffer
     }
     S.seq += (unsigned)ntiles;
     return true;
@@ -362,7 +380,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             if (!replaced_rw && stg) {
                 // staged: r s z p v r0 through shared memory, w (SpMV) from global
                 const float *src[kStageVecs] = {V.r, V.s, V.z, V.p, V.v, V.r0};
-                const bool ok = staged_sweep(*stg, src, lo, hi, [&](const float *tb, int row0) {
+                const bool ok = staged_sweep<float, kStageVecs>(*stg, src, lo, hi, [&](const float *tb, int row0) {
                     const int j = 2 * (int)threadIdx.x;
                     const int i0 = row0 + j;
                     if (i0 >= hi) return;
@@ -515,7 +533,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             if (!replace_now && stg) {
                 // staged: q y x p t r0 through shared memory, z (SpMV) from global
                 const float *src[kStageVecs] = {V.q, V.y, x, V.p, V.t, V.r0};
-                const bool ok = staged_sweep(*stg, src, lo, hi, [&](const float *tb, int row0) {
+                const bool ok = staged_sweep<float, kStageVecs>(*stg, src, lo, hi, [&](const float *tb, int row0) {
                     const int j = 2 * (int)threadIdx.x;
                     const int i0 = row0 + j;
                     if (i0 >= hi) return;
@@ -1182,18 +1200,21 @@ template <class Op64, class Op32>
 __global__ void __launch_bounds__(kTPB, 9) mixed_kernel(const Op64 A, const Op32 A32, const MixedArgs m) {
     __shared__ double sm[kMaxDots][32];
     __shared__ int sflag;
-    __shared__ uint64_t stage_bar[kStages];
-    extern __shared__ __align__(128) float stage_buf[];   // kStageSmemBytes when the sweeps are staged
+    __shared__ uint64_t stage_full[kStages], stage_empty[kStages];
+    extern __shared__ __align__(128) char stage_buf[];   // kStageSmemBytes when the sweeps are staged
     constexpr bool kStaged = HasRow2<Op32>::value;
     if (threadIdx.x == 0) {
         sflag = 1;   // read only after the first exchange's barrier
         if (kStaged) {
-            for (int k = 0; k < kStages; ++k) mbar_init(&stage_bar[k], 1);
+            for (int k = 0; k < kStages; ++k) {
+                mbar_init(&stage_full[k], 1);
+                mbar_init(&stage_empty[k], kTPB);
+            }
             mbar_init_fence();
         }
     }
     __syncthreads();
-    Stager stager{stage_buf, stage_bar, 0u, m.ctl};
+    Stager stager{stage_buf, stage_full, stage_empty, 0u, m.ctl};
     GridSync g{m.ctl, m.partials, 0u, 0};
     // row ranges start on multiples of 4 rows: the FP32 sweeps access rows in
     // aligned pairs, and the staged ones copy 16-byte aligned tiles

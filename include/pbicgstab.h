@@ -288,8 +288,16 @@ typedef struct {
  * Zero fields take the defaults. */
 typedef struct {
     int32_t cluster_size;       /* CTAs per cluster: 1 (no clusters), 2, 4, 8 or 16; 0 = 8 */
-    int32_t pad;
+    int32_t fixed_iters;        /* > 0: every system runs exactly this many iterations and
+                                   ignores rtol (breakdown still stops); for step-by-step
+                                   comparison (default 0) */
     int64_t cluster_min_rows;   /* systems with at least this many rows use a whole cluster; 0 = 512 */
+    double *d_history;          /* NULL, or device buffer of nsys * history_stride doubles:
+                                   ||r_i||_2 of system s's recursive residual at
+                                   d_history[s * history_stride + i], i = 0..its iterations;
+                                   entries past them are untouched (default NULL) */
+    int64_t history_stride;     /* >= (fixed_iters > 0 ? fixed_iters : maxit) + 1 when
+                                   d_history is set (PBCG_ERR_ARG otherwise) */
 } pbcg_batch_opts;
 
 /* Workspace of a batched solve: 10 FP64 vectors over all rows + a counter. */

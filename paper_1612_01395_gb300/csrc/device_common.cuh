@@ -192,6 +192,11 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// The block that records per-solve results (the residual history) under each
+// synchronisation policy: block 0 of a grid; the block itself when a block
+// solves alone; CTA rank 0 of a cluster (is_leader overloads below).
+__device__ __forceinline__ bool is_leader(const GridSync &) { return blockIdx.x == 0; }
+
 // Thread 0: spin until *word >= target, bounded; false on abort or timeout.
 __device__ __forceinline__ bool wait_at_least(GridSync &g, const unsigned *word, unsigned target) {
     const uint64_t t0 = globaltimer_ns();
@@ -294,6 +299,8 @@ __device__ __forceinline__ bool grid_sum(GridSync &g, double (&v)[K], double (*s
 struct BlockSync {
     int count;
 };
+
+__device__ __forceinline__ bool is_leader(const BlockSync &) { return true; }
 
 __device__ __forceinline__ bool grid_sync(BlockSync &g, double (*)[32], int *) {
     __syncthreads();
@@ -426,6 +433,8 @@ struct ClusterSync {
     unsigned epoch;     // reductions done
     int count;
 };
+
+__device__ __forceinline__ bool is_leader(const ClusterSync &g) { return g.rank == 0; }
 
 __device__ __forceinline__ bool grid_sync(ClusterSync &g, double (*)[32], int *) {
     cluster_barrier();

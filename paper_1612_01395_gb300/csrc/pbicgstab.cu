@@ -801,6 +801,12 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     if (csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)
         return fail(PBCG_ERR_ARG, "cluster_size must be 1, 2, 4, 8 or 16 (got %d)", csize);
     if (cmin < 0) return fail(PBCG_ERR_ARG, "cluster_min_rows must be >= 0");
+    const int fixed = opts ? opts->fixed_iters : 0;
+    double *hist = opts ? opts->d_history : nullptr;
+    const long long hstride = opts ? opts->history_stride : 0;
+    if (fixed < 0) return fail(PBCG_ERR_ARG, "fixed_iters must be >= 0");
+    if (hist && hstride < (long long)(fixed > 0 ? fixed : maxit) + 1)
+        return fail(PBCG_ERR_ARG, "history_stride must be >= (fixed_iters > 0 ? fixed_iters : maxit) + 1");
     cudaStream_t st = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     PBCG_CUDA(cudaGetDevice(&dev));
@@ -825,6 +831,9 @@ extern "C" pbcg_status pbicgstab_solve_batched(const pbcg_batch *batch, int64_t 
     B.maxit = maxit;
     B.replace_period = replace_period;
     B.cluster_min_rows = cmin;
+    B.fixed = fixed;
+    B.hist = hist;
+    B.hist_stride = hstride;
 
     // One resident wave of clusters; clusters take systems until none is left.
     cudaLaunchConfig_t cfg = {};

@@ -93,13 +93,52 @@ __device__ __forceinline__ bool norm_below(double sq, double tol, double tol2) {
     return (sq <= 2.0 * tol2 || !(tol2 >= 2.2250738585072014e-308)) && sqrt(sq) <= tol;
 }
 
+// The divisions of an iteration's scalar updates are evaluated once per block,
+// by one warp each, and shared through shared memory. An FP64 warp
+// instruction occupies its sub-partition's FP64 pipe for 64 cycles whether
+// one warp or all four compute the same scalar, so with several resident
+// blocks per SM the redundant copies queued on the same pipes, on the
+// critical path between two sweeps. The warp is rotated by the block index,
+// (blockIdx.x + k) mod 4, so the resident blocks spread their divisions over
+// the four sub-partitions. Every thread receives the same bits as before.
+// sq: a row of 32 shared doubles; slots 0-1 beta, 2-3 den and alpha, 4 omega.
+__device__ __forceinline__ int scalar_warp(int k) { return (int)((blockIdx.x + (unsigned)k) % (kTPB / 32)); }
+
+// a / b on one warp, returned to every thread (the slot is rewritten only
+// after later barriers).
+__device__ __forceinline__ double div_shared(double a, double b, int warp, double *slot) {
+    if ((int)(threadIdx.x >> 5) == warp) {
+        const double q = __ddiv_rn(a, b);
+        if ((threadIdx.x & 31) == 0) *slot = q;
+    }
+    __syncthreads();
+    return *slot;
+}
+
+// Denominator of eq. (3), r0w + beta r0s - beta omega r0z, and alpha_{i+1} =
+// rho_n / den (only when den != 0) on one warp; both returned to every thread.
+__device__ __forceinline__ void alpha_shared(double rho_n, double r0w, double r0s, double r0z, double beta,
+                                             double omega, double *sq, double &den, double &alpha) {
+    if ((int)(threadIdx.x >> 5) == scalar_warp(2)) {
+        const double d = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
+        const double al = d == 0.0 ? 0.0 : __ddiv_rn(rho_n, d);
+        if ((threadIdx.x & 31) == 0) {
+            sq[2] = d;
+            sq[3] = al;
+        }
+    }
+    __syncthreads();
+    den = sq[2];
+    alpha = sq[3];
+}
+
 // beta = (alpha / omega) (rho_n / rho): the two divisions are independent, so
-// warps 0 and 1 evaluate one each (every warp has its own FP64 pipe) and share
+// two warps evaluate one each (every warp has its own FP64 pipe) and share
 // them through shared memory.
 __device__ __forceinline__ double beta_of(double alpha, double omega, double rho_n, double rho, double *sq) {
     const int wid = threadIdx.x >> 5;
-    if (wid == 0) sq[0] = __ddiv_rn(alpha, omega);
-    if (wid == 1) sq[1] = __ddiv_rn(rho_n, rho);
+    if (wid == scalar_warp(0)) sq[0] = __ddiv_rn(alpha, omega);
+    if (wid == scalar_warp(1)) sq[1] = __ddiv_rn(rho_n, rho);
     __syncthreads();
     const double b = __dmul_rn(sq[0], sq[1]);
     __syncthreads();
@@ -349,7 +388,7 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
     double rho = d0[0];                 // (r0, r_0)
     o.nr0 = sqrt(rho);
     o.nr = o.nr0;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[0] = o.nr0;
+    if (threadIdx.x == 0 && a.hist && is_leader(g)) a.hist[0] = o.nr0;
     const double tol = __dmul_rn(a.rtol, o.nr0), tol2 = __dmul_rn(tol, tol);
     if (o.nr0 == 0.0) { o.status = PBCG_OK; return true; }
 
@@ -517,10 +556,10 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
             o.nr = qq;
             o.half = 1;
             o.status = PBCG_OK;
-            if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
+            if (threadIdx.x == 0 && a.hist && is_leader(g)) a.hist[it] = qq;
             break;
         }
-        omega = __ddiv_rn(qy, yy);
+        omega = div_shared(qy, yy, scalar_warp(3), &sm[kMaxDots - 1][4]);
         if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
 
         // ---- phase B: v_i = A z_i; x_{i+1}, r_{i+1}, w_{i+1}; second reduction
@@ -640,15 +679,15 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
         ++it;
         const double rho_n = d2[0], r0w = d2[1];
         o.nr = d2[2];
-        if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = d2[2];
+        if (threadIdx.x == 0 && a.hist && is_leader(g)) a.hist[it] = d2[2];
         if (!all_finite(d2)) { o.status = PBCG_NONFINITE; break; }
         if (!fixed && norm_below(d2[2], tol, tol2)) { o.status = PBCG_OK; break; }
         if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
         // beta_i = (alpha_i / omega_i) (r0, r_{i+1}) / (r0, r_i); alpha_{i+1} by eq. (3)
         beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
-        const double den = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
+        double den;
+        alpha_shared(rho_n, r0w, r0s, r0z, beta, omega, sm[kMaxDots - 1], den, alpha);
         if (den == 0.0) { o.status = PBCG_BREAKDOWN; break; }
-        alpha = __ddiv_rn(rho_n, den);
         rho = rho_n;
     }
     o.iters = it;
@@ -940,7 +979,7 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, S
         if (!grid_sum<1>(g, d1, sm, sflag)) return false;
         if (!isfinite(d1[0])) { o.status = PBCG_NONFINITE; break; }
         if (d1[0] == 0.0) { o.status = PBCG_BREAKDOWN; break; }
-        const double alpha = __ddiv_rn(rho, d1[0]);
+        const double alpha = div_shared(rho, d1[0], scalar_warp(2), &sm[kMaxDots - 1][3]);
 
         // ---- q_i = r_i - alpha s_i; y_i = A q_i; omega_i
         double d2[3] = {0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q)
@@ -983,7 +1022,7 @@ __device__ __forceinline__ bool standard_loop(const Op &A, const SolveArgs &a, S
             if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
             break;
         }
-        omega = __ddiv_rn(qy, yy);
+        omega = div_shared(qy, yy, scalar_warp(3), &sm[kMaxDots - 1][4]);
         if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
 
         // ---- x_{i+1}, r_{i+1}; beta_i
@@ -1401,6 +1440,9 @@ struct BatchArgs {
     int maxit;
     int replace_period;
     long long cluster_min_rows;    // systems this large are solved by a whole cluster
+    int fixed;                     // > 0: every system runs exactly this many iterations
+    double *hist;                  // nullable: ||r_i|| of system s at hist[s * hist_stride + i]
+    long long hist_stride;
 };
 
 // Solve system `sys` on rows [lo, hi) of it (the whole system for BlockSync,
@@ -1433,10 +1475,10 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
                       B.V.q + r0, B.V.y + r0, B.V.w + r0, B.V.t + r0, B.V.v + r0};
         a.ctl = nullptr;
         a.partials = nullptr;
-        a.hist = nullptr;
+        a.hist = B.hist ? B.hist + (size_t)sys * (size_t)B.hist_stride : nullptr;
         a.rtol = B.rtol;
-        a.limit = B.maxit;
-        a.fixed = 0;
+        a.limit = B.fixed > 0 ? B.fixed : B.maxit;
+        a.fixed = B.fixed > 0 ? 1 : 0;
         a.replace_period = B.replace_period;
         a.max_repl = -1;
         a.variant = 0;
@@ -1445,6 +1487,9 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
         Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
         int spmvs = 0;
         pipelined_loop<CsrOpScalar, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
+        // the history holds squared norms after entry 0 (written by this thread)
+        if (a.hist && part == 0 && threadIdx.x == 0)
+            for (int i = 1; i <= o.iters; ++i) a.hist[i] = sqrt(a.hist[i]);
         // true residual of the returned x
         double d[1] = {0.0};
         PBCG_ROWS(i) {

@@ -85,7 +85,9 @@ class PbcgBatch(ctypes.Structure):
 
 
 class PbcgBatchOpts(ctypes.Structure):
-    _fields_ = [("cluster_size", ctypes.c_int32), ("pad", ctypes.c_int32), ("cluster_min_rows", ctypes.c_int64)]
+    _fields_ = [("cluster_size", ctypes.c_int32), ("fixed_iters", ctypes.c_int32),
+                ("cluster_min_rows", ctypes.c_int64), ("d_history", ctypes.c_void_p),
+                ("history_stride", ctypes.c_int64)]
 
 
 class PbcgBatchResult(ctypes.Structure):
@@ -306,12 +308,15 @@ class BatchSolver:
         self._np = np
 
     def launch(self, b, x, rtol=1e-8, maxit=1000, replace_period=0, stream=None, cluster_size=0,
-               cluster_min_rows=0):
+               cluster_min_rows=0, fixed_iters=0, history=None):
         """Enqueue the batched solve (asynchronous). cluster_size / cluster_min_rows:
-        the launch shape (0 = library defaults)."""
+        the launch shape (0 = library defaults). fixed_iters > 0 runs every system
+        exactly that many iterations; history: a float64 CUDA tensor of shape
+        (nsys, stride) receiving each system's residual norms."""
         torch = self.torch
         st = (stream or torch.cuda.current_stream()).cuda_stream
-        opts = PbcgBatchOpts(int(cluster_size), 0, int(cluster_min_rows))
+        hp, hs = (history.data_ptr(), history.shape[1]) if history is not None else (None, 0)
+        opts = PbcgBatchOpts(int(cluster_size), int(fixed_iters), int(cluster_min_rows), hp, int(hs))
         rc = pbicgstab_solve_batched(self.desc, self.total, b.data_ptr(), x.data_ptr(), rtol, maxit, replace_period,
                                      opts, self.ws_ptr, self.ws_bytes, self.results.data_ptr(), st)
         if rc != PBCG_OK:

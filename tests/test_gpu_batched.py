@@ -178,3 +178,55 @@ def test_degenerate_systems_in_a_batch(shape):
         r0, r1 = int(B.row_offset[k]), int(B.row_offset[k + 1])
         exact = np.linalg.solve(A.to_dense(), B.b[r0:r1])
         assert np.linalg.norm(xg[r0:r1] - exact) <= 1e-9 * np.linalg.norm(exact), k
+
+
+@pytest.mark.parametrize("shape", [(1, 0), (8, 1), (4, 1000)], ids=["alone", "cluster8", "mixed4"])
+def test_batched_first_iterations_match_oracle(shape):
+    """Every system of a batch, step by step against the oracle's Algorithm 9
+    on that system: residual norms within 1e-8 and x within 1e-9, whether the
+    system is solved by one CTA or by a cluster, without replacement (12
+    iterations) and with replacement every 5 (10 iterations, so the window
+    ends on a replaced entry, whose bar adds ||A (x_gpu - x_oracle)||: the
+    true residuals of two x that differ by dx differ by up to that).
+
+    The horizon is the one these systems allow any correct FP64
+    implementation: they converge by about 8 orders in 20 iterations, and two
+    correct summation orders (the C oracle's Algorithms 7 and 9, and a numpy
+    Algorithm 9) differ in ||r_i|| by 1e-9 at iteration 12, 2e-8 at 14 and
+    1e-5 at 19 on them."""
+    import torch
+    B = P.random_batch(nsys=10, seed=4, nmin=300, nmax=3000)
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    for rr, K in ((0, 12), (5, 10)):
+        x = torch.zeros_like(b)
+        hist = torch.full((B.nsys, K + 1), float("nan"), dtype=torch.float64, device="cuda")
+        bs.launch(b, x, rtol=0.0, maxit=K, replace_period=rr, cluster_size=shape[0], cluster_min_rows=shape[1],
+                  fixed_iters=K, history=hist)
+        res = bs.fetch_results()
+        xg, hg = x.cpu().numpy(), hist.cpu().numpy()
+        for s in range(B.nsys):
+            A = B.system(s)
+            r0, r1 = B.row_offset[s], B.row_offset[s + 1]
+            ref = oracle.pbicgstab(A, B.b[r0:r1], rtol=0.0, maxit=K, fixed_iters=K, replace_period=rr)
+            assert res["status"][s] == native.PBCG_OK and res["iters"][s] == K, (s, res[s])
+            assert res["n_replacements"][s] == ref.n_replacements
+            xs = xg[r0:r1]
+            tol = 1e-8 * ref.hist + 1e-13 * ref.nr0
+            if rr:
+                tol[-1] += np.linalg.norm(oracle.spmv(A, xs - ref.x))
+            assert np.all(np.abs(hg[s] - ref.hist) <= tol), (s, np.abs(hg[s] - ref.hist) / ref.hist)
+            assert np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x) <= 1e-9, s
+
+
+def test_batched_history_arguments_are_checked():
+    import torch
+    B = P.random_batch(nsys=2, seed=4, nmin=300, nmax=400)
+    bs = native.BatchSolver(B)
+    b = torch.from_numpy(B.b).cuda()
+    x = torch.zeros_like(b)
+    short = torch.zeros((B.nsys, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(native.PbcgError):
+        bs.launch(b, x, rtol=0.0, maxit=20, fixed_iters=20, history=short)
+    with pytest.raises(native.PbcgError):
+        bs.launch(b, x, rtol=1e-8, maxit=100, fixed_iters=-1)

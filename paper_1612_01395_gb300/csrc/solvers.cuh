@@ -698,12 +698,17 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
 // ===========================================================================
 // Algorithm 11 (preconditioned pipelined BiCGStab) with a diagonal M^{-1},
 // applied elementwise inside the sweeps, so an iteration still takes two
-// grid-wide exchanges: phase A forms z^ = M^{-1} z next to z, phase B forms
-// w^ = M^{-1} w next to w, and each SpMV reads the hat vector the previous
-// phase wrote (t = A w^, v = A z^). Residual replacement (Section 4.2) as in
-// the unpreconditioned loop: r := b - A x, r^ := M^{-1} r, w := A r^ before the
-// second reduction of iteration i-1; s := A p^, s^ := M^{-1} s, z := A s^
-// after p^_i. V.p holds p^.
+// grid-wide exchanges. The hat vectors of Algorithm 11 are M^{-1} times their
+// plain counterparts (r^ = M^{-1} r, s^ = M^{-1} s, q^ = M^{-1} q, z^, w^);
+// the algorithm carries r^, s^, q^ as recurrences because applying a general
+// M^{-1} costs a solve. With a diagonal M^{-1} it costs one product, so this
+// loop forms r^, s^, q^ where they are used (m_i r_i, m_i s_i, m_i q_i) and
+// stores only the hat vectors an SpMV reads: z^ (v = A z^) and w^ (t = A w^),
+// plus p^ (V.p). That removes the r^, s^, q^ recurrences and their 48 bytes
+// per unknown and iteration of traffic; in exact arithmetic the iterates are
+// Algorithm 11's. Residual replacement (Section 4.2): r := b - A x and
+// w := A r^ before the second reduction of iteration i-1; s := A p^ and
+// z := A s^ after p^_i; r^ and s^ are then stored as SpMV inputs (rh, sh).
 // ===========================================================================
 template <class Op>
 __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs &a, GridSync &g, double (*sm)[32],
@@ -711,10 +716,10 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
     const Vectors &V = a.V;
     double *x = a.x;
     const double *mi = a.minv;
-    double *rh = a.rh, *sh = a.sh, *zh = a.zh, *qh = a.qh, *wh = a.wh;
+    double *rh = a.rh, *sh = a.sh, *zh = a.zh, *wh = a.wh;
     const bool fixed = a.fixed != 0;
 
-    // r_0 := b - A x_0; r0 := r_0; r^_0 := M^{-1} r_0; p^, s, s^, z, z^, v := 0
+    // r_0 := b - A x_0; r0 := r_0; r^_0 := M^{-1} r_0 (an SpMV input); p^, s, z, v := 0
     double d0[1] = {0.0};
     PBCG_ROWS(i) {
         const double ri = a.b[i] - A.row(i, VecLoad{x});
@@ -723,9 +728,7 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
         rh[i] = mi[i] * ri;
         V.p[i] = 0.0;
         V.s[i] = 0.0;
-        sh[i] = 0.0;
         V.z[i] = 0.0;
-        zh[i] = 0.0;
         V.v[i] = 0.0;
         d0[0] = fma(ri, ri, d0[0]);
     }
@@ -755,27 +758,23 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
     bool replaced = false;
     int it = 0;
     while (it < a.limit) {
-        // ---- phase A: t = A w^; p^, s, s^, z, q, q^, y, z^; first reduction
+        // ---- phase A: t = A w^; p^, s, z, z^, q, y; first reduction
         double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // (q,y) (y,y) (q,q) (r0,s) (r0,z)
         if (!replaced) {
             PBCG_ROWS(i) {
                 const double ti = A.row(i, VecLoad{wh});
-                const double si = V.s[i], zi = V.z[i], shi = sh[i];
-                const double ph = fma(beta, fma(-omega, shi, V.p[i]), rh[i]);   // p^_i
-                const double sn = fma(beta, fma(-omega, zi, si), V.w[i]);       // s_i
-                const double shn = fma(beta, fma(-omega, zh[i], shi), wh[i]);   // s^_i
-                const double zn = fma(beta, fma(-omega, V.v[i], zi), ti);       // z_i
-                const double qi = fma(-alpha, sn, V.r[i]);                      // q_i
-                const double qhi = fma(-alpha, shn, rh[i]);                     // q^_i
-                const double yi = fma(-alpha, zn, V.w[i]);                      // y_i
+                const double m = mi[i], ri = V.r[i], si = V.s[i], zi = V.z[i], wi = V.w[i];
+                const double ph = fma(beta, fma(-omega, m * si, V.p[i]), m * ri);   // p^_i = r^_i + beta (p^ - omega s^)
+                const double sn = fma(beta, fma(-omega, zi, si), wi);               // s_i
+                const double zn = fma(beta, fma(-omega, V.v[i], zi), ti);           // z_i
+                const double qi = fma(-alpha, sn, ri);                              // q_i
+                const double yi = fma(-alpha, zn, wi);                              // y_i
                 V.t[i] = ti;
                 V.p[i] = ph;
                 V.s[i] = sn;
-                sh[i] = shn;
                 V.z[i] = zn;
-                zh[i] = mi[i] * zn;                                             // z^_i
+                zh[i] = m * zn;                                                     // z^_i
                 V.q[i] = qi;
-                qh[i] = qhi;
                 V.y[i] = yi;
                 const double r0i = V.r0[i];
                 d1[0] = fma(qi, yi, d1[0]);
@@ -786,9 +785,11 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
             }
             ++spmvs;
         } else {
+            // replacement, second part: t = A w^ (w^ replaced), p^; then s := A p^, s^ := M^{-1} s, z := A s^
             PBCG_ROWS(i) {
+                const double m = mi[i];
                 V.t[i] = A.row(i, VecLoad{wh});
-                V.p[i] = fma(beta, fma(-omega, sh[i], V.p[i]), rh[i]);
+                V.p[i] = fma(beta, fma(-omega, m * V.s[i], V.p[i]), m * V.r[i]);   // r^ = M^{-1} r replaced
             }
             if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
@@ -801,12 +802,10 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
                 const double zn = A.row(i, VecLoad{sh});
                 const double sn = V.s[i];
                 const double qi = fma(-alpha, sn, V.r[i]);
-                const double qhi = fma(-alpha, sh[i], rh[i]);
                 const double yi = fma(-alpha, zn, V.w[i]);
                 V.z[i] = zn;
                 zh[i] = mi[i] * zn;
                 V.q[i] = qi;
-                qh[i] = qhi;
                 V.y[i] = yi;
                 const double r0i = V.r0[i];
                 d1[0] = fma(qi, yi, d1[0]);
@@ -832,26 +831,24 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
             if (blockIdx.x == 0 && threadIdx.x == 0 && a.hist) a.hist[it] = qq;
             break;
         }
-        omega = __ddiv_rn(qy, yy);
+        omega = div_shared(qy, yy, scalar_warp(3), &sm[kMaxDots - 1][4]);
         if (omega == 0.0) { o.status = PBCG_BREAKDOWN; break; }
 
-        // ---- phase B: v = A z^; x, r, r^, w, w^; second reduction
+        // ---- phase B: v = A z^; x, r, w, w^; second reduction
         const bool replace_now = a.replace_period > 0 && (it + 1) % a.replace_period == 0 &&
                                  (a.max_repl < 0 || o.nrr < a.max_repl);
         double d2[3] = {0.0, 0.0, 0.0};   // (r0,r) (r0,w) (r,r)
         if (!replace_now) {
             PBCG_ROWS(i) {
                 const double vi = A.row(i, VecLoad{zh});
-                const double qi = V.q[i], yi = V.y[i];
-                x[i] = fma(omega, qh[i], fma(alpha, V.p[i], x[i]));
+                const double m = mi[i], qi = V.q[i], yi = V.y[i];
+                x[i] = fma(omega, m * qi, fma(alpha, V.p[i], x[i]));   // x + alpha p^ + omega q^
                 const double rn = fma(-omega, yi, qi);
-                const double rhn = fma(-omega, fma(-alpha, zh[i], wh[i]), qh[i]);
                 const double wn = fma(-omega, fma(-alpha, vi, V.t[i]), yi);
                 V.v[i] = vi;
                 V.r[i] = rn;
-                rh[i] = rhn;
                 V.w[i] = wn;
-                wh[i] = mi[i] * wn;
+                wh[i] = m * wn;                                         // w^_{i+1}
                 const double r0i = V.r0[i];
                 d2[0] = fma(r0i, rn, d2[0]);
                 d2[1] = fma(r0i, wn, d2[1]);
@@ -859,7 +856,7 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
             }
             ++spmvs;
         } else {
-            PBCG_ROWS(i) { x[i] = fma(omega, qh[i], fma(alpha, V.p[i], x[i])); }
+            PBCG_ROWS(i) { x[i] = fma(omega, mi[i] * V.q[i], fma(alpha, V.p[i], x[i])); }
             if (!grid_sync(g, sm, sflag)) return false;
             PBCG_ROWS(i) {
                 const double rn = a.b[i] - A.row(i, VecLoad{x});
@@ -889,9 +886,9 @@ __device__ __forceinline__ bool pipelined_prec_loop(const Op &A, const SolveArgs
         if (!fixed && norm_below(d2[2], tol, tol2)) { o.status = PBCG_OK; break; }
         if (rho_n == 0.0) { o.status = PBCG_BREAKDOWN; break; }
         beta = beta_of(alpha, omega, rho_n, rho, sm[kMaxDots - 1]);
-        const double den = __dsub_rn(__dadd_rn(r0w, __dmul_rn(beta, r0s)), __dmul_rn(__dmul_rn(beta, omega), r0z));
+        double den;
+        alpha_shared(rho_n, r0w, r0s, r0z, beta, omega, sm[kMaxDots - 1], den, alpha);
         if (den == 0.0) { o.status = PBCG_BREAKDOWN; break; }
-        alpha = __ddiv_rn(rho_n, den);
         rho = rho_n;
     }
     o.iters = it;

@@ -90,3 +90,17 @@ def test_bounds_checked_build_compiles_and_exports():
     L = ctypes.CDLL(path)
     for name in native.EXPORTS:
         assert hasattr(L, name), name
+
+
+def test_batched_option_errors_need_no_gpu(lib):
+    """Host-side checks of the batched options run before any CUDA call."""
+    batch = native.PbcgBatch(1, 4, 256, 512, 768, 1024)   # fake device addresses, never dereferenced
+    ws_bytes = native.pbicgstab_batched_workspace_bytes(4)
+    res = native.PbcgBatchResult()
+    for opts, msg in ((native.PbcgBatchOpts(1, -1, 0, None, 0), "fixed_iters"),
+                      (native.PbcgBatchOpts(1, 20, 0, 4096, 10), "history_stride"),
+                      (native.PbcgBatchOpts(3, 0, 0, None, 0), "cluster_size")):
+        st = lib.pbicgstab_solve_batched(ctypes.byref(batch), 4, 256, 512, 1e-8, 100, 0, ctypes.byref(opts), 4096,
+                                         ws_bytes, ctypes.addressof(res), None)
+        assert st == native.PBCG_ERR_ARG, msg
+        assert msg in native.pbicgstab_last_error()

@@ -111,7 +111,9 @@ typedef struct {
                                  points x unknowns -- are solved by one thread-block cluster,
                                  larger ones by a cooperative grid); -1 = always the
                                  cooperative grid; 2, 4, 8 or 16 = one cluster of that many CTAs
-                                 (default 0; ignored when grid > 0) */
+                                 (default 0; ignored when grid > 0). A PBCG_PREC_JACOBI handle
+                                 always takes the grid, and a positive value, or a size the
+                                 device cannot make resident, returns PBCG_ERR_ARG */
     int32_t stall_steps;      /* pbicgstab_solve_mixed only: stop (PBCG_NOT_CONVERGED) after this
                                  many refinement steps in a row that fail to bring the FP64
                                  residual below the best one so far; 0 = the default, 6 (converging

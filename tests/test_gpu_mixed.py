@@ -256,3 +256,33 @@ def test_converging_refinement_is_not_stopped_by_the_stall_rule():
     true_rel = np.linalg.norm(b - oracle.spmv(A, x.cpu().numpy())) / np.linalg.norm(b)
     assert true_rel <= 1e-10
     s.close()
+
+
+def tiny_stencil(nx, ny, nz):
+    if nz == 1 and ny == nx and nx > 1:
+        return P.cd2d_constant(nx, (10.0, 10.0))
+    if nx == ny == nz:
+        return P.cd3d_trig(nx)
+    return P.convection_diffusion((nx, ny, nz), (np.full(ny, 20.0), np.full(nz, 5.0), np.full(nx, 10.0)))
+
+
+@pytest.mark.parametrize("dims", [(3, 1, 1), (7, 1, 1), (2, 2, 1), (3, 3, 1), (2, 2, 2), (3, 3, 3), (5, 5, 5),
+                                  (9, 9, 1)])
+def test_mixed_stencil_tiny_and_ragged_tiles(dims):
+    """The staged FP32 sweeps copy tiles of 256 rows rounded up to 16 bytes:
+    systems of 3 to 125 rows have a single partial tile, odd tails and x-lines
+    of odd length (so row pairs fall back to single rows). Each must reach a
+    1e-10 true residual (recomputed by the oracle's SpMV) and agree with the
+    oracle's FP64 solution."""
+    st = tiny_stencil(*dims)
+    A = P.stencil_to_csr(st)
+    b = oracle.spmv(A, P.splitmix64_uniform(0, A.n))
+    s = native.Solver.from_stencil(st)
+    x, info = s.solve_mixed(dev(b), None, native.PBCG_VALUES_F32, rtol=1e-10, max_outer=30, inner_rtol=1e-3,
+                            inner_maxit=200)
+    assert info["status"] == native.PBCG_OK, info
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(b - oracle.spmv(A, xg)) <= 1e-10 * np.linalg.norm(b)
+    ref = oracle.pbicgstab(A, b, rtol=1e-13, maxit=2000, replace_period=20)
+    assert np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x) <= 1e-8
+    s.close()

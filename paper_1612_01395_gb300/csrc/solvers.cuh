@@ -1453,7 +1453,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
     int bad = (r0 < 0 || r1 < r0 || r1 > B.total_rows || r1 - r0 >= (1ll << 31)) ? 1 : 0;
     const int n = bad ? 0 : (int)(r1 - r0);
     const int lo = (int)((long long)part * n / parts), hi = (int)((long long)(part + 1) * n / parts);
-    const CsrOpScalar A{n, B.rowptr + (bad ? 0 : r0), B.col, B.val, B.nnz};
+    const CsrOpGatherL2 A{{n, B.rowptr + (bad ? 0 : r0), B.col, B.val, B.nnz}};
     PBCG_ROWS(i) {
         const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
         if (e0 < 0 || e1 < e0 || e1 > B.nnz) { bad = 1; continue; }
@@ -1483,7 +1483,7 @@ __device__ __forceinline__ void batched_system(const BatchArgs &B, int sys, Sync
         a.rh = a.sh = a.zh = a.qh = a.wh = nullptr;
         Outcome o{0, PBCG_NOT_CONVERGED, 0, 0, 0.0, 0.0};
         int spmvs = 0;
-        pipelined_loop<CsrOpScalar, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
+        pipelined_loop<CsrOpGatherL2, double, Sync>(A, a, g, sm, sflag, lo, hi, o, spmvs);
         // the history holds squared norms after entry 0 (written by this thread)
         if (a.hist && part == 0 && threadIdx.x == 0)
             for (int i = 1; i <= o.iters; ++i) a.hist[i] = sqrt(a.hist[i]);

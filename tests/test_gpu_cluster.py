@@ -4,8 +4,8 @@ Systems of up to 24576 stored entries (stencil: points x unknowns) are solved
 by default by the CTAs of one thread-block cluster, whose reductions go through distributed shared memory
 and the hardware cluster barrier instead of a cooperative grid's exchanges
 through L2. The solver loops are the same code; only the reduction tree (and
-so the rounding of the dot products) differs. The oracle judges it as it
-judges the grid: residual norms within 1e-8 and x within 1e-9 over the first
+so the rounding of the dot products) differs. It is held against the oracle
+as the grid is: residual norms within 1e-8 and x within 1e-9 over the first
 20 iterations, for every cluster size and both methods, and final solutions
 of tight solves within 1e-9.
 """

@@ -128,10 +128,14 @@ struct L2Gather<VecLoadT<T>> {
 };
 
 // The batched solver's CSR operator (random systems, 9-33 entries a row with
-// uniformly random columns): its gathers go through L2 only, which leaves L1
-// to the lanes' streams of column indices and values, each of whose sectors
-// serves 4 to 8 consecutive entries. 52.4 against 55.1 ms for the 512-system
-// batch, bit for bit the same results.
+// uniformly random columns). Each lane streams its own row's column indices
+// and values, and a sector of them serves 4 to 8 consecutive entries if it
+// stays in L1 that long. So everything else bypasses L1 (ld.global.cg, cached
+// in L2 only): the SpMV's gathers, and the fused sweeps' vector loads, which
+// are used once (SweepLoadsL2). On the 512-system batch, the gathers alone
+// took 52.4 against 55.1 ms, the gathers and sweep loads 50.6 against 52.8
+// ms; an evict_last priority on the row streams' loads changed nothing
+// (52.4 ms). The results are bit for bit the same.
 struct CsrOpGatherL2 : CsrOpScalar {
     template <class L>
     __device__ __forceinline__ auto row(int r, const L &u) const -> decltype(u(0)) {
@@ -303,6 +307,16 @@ struct StencilOpT {
     }
 };
 using StencilOp = StencilOpT<double>;
+
+// Operators whose fused sweeps load their vectors through L2 only.
+template <class Op>
+struct SweepLoadsL2 {
+    static constexpr bool value = false;
+};
+template <>
+struct SweepLoadsL2<CsrOpGatherL2> {
+    static constexpr bool value = true;
+};
 
 // Operators with row2 (pairs of FP32 rows).
 template <class Op>

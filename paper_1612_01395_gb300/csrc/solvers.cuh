@@ -239,6 +239,17 @@ __device__ __forceinline__ void load_group(const T *p, int i, int cnt, T (&out)[
 #pragma unroll
     for (int u = 0; u < G; ++u) out[u] = u < cnt ? p[i + u] : T(0);
 }
+// load_group for a fused sweep: through L2 only (ld.global.cg) for operators
+// whose sweeps leave L1 to their SpMV's row streams.
+template <class Op, int G, typename T>
+__device__ __forceinline__ void load_sweep(const T *p, int i, int cnt, T (&out)[G]) {
+    if constexpr (SweepLoadsL2<Op>::value) {
+#pragma unroll
+        for (int u = 0; u < G; ++u) out[u] = u < cnt ? __ldcg(p + i + u) : T(0);
+    } else {
+        load_group(p, i, cnt, out);
+    }
+}
 template <int G, typename T>
 __device__ __forceinline__ void store_group(T *p, int i, int cnt, const T (&in)[G]) {
     if constexpr (G == 2 && sizeof(T) == 4) {
@@ -485,13 +496,13 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                     for (int u = 0; u < kGroup; ++u)
                         if (u < cnt) ti[u] = A.row(i0 + u, VecLoadT<T>{V.w});
                 }
-                load_group(V.r, i0, cnt, ri);
-                load_group(V.w, i0, cnt, wi);
-                load_group(V.s, i0, cnt, si);
-                load_group(V.z, i0, cnt, zi);
-                load_group(V.p, i0, cnt, pi);
-                load_group(V.v, i0, cnt, vi);
-                load_group(V.r0, i0, cnt, r0i);
+                load_sweep<Op>(V.r, i0, cnt, ri);
+                load_sweep<Op>(V.w, i0, cnt, wi);
+                load_sweep<Op>(V.s, i0, cnt, si);
+                load_sweep<Op>(V.z, i0, cnt, zi);
+                load_sweep<Op>(V.p, i0, cnt, pi);
+                load_sweep<Op>(V.v, i0, cnt, vi);
+                load_sweep<Op>(V.r0, i0, cnt, r0i);
                 T pn[kGroup], sn[kGroup], zn[kGroup], qn[kGroup], yn[kGroup];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {
@@ -631,12 +642,12 @@ __device__ __forceinline__ bool pipelined_loop(const Op &A, const SolveArgsT<T> 
                     for (int u = 0; u < kGroup; ++u)
                         if (u < cnt) vi[u] = A.row(i0 + u, VecLoadT<T>{V.z});
                 }
-                load_group(V.q, i0, cnt, qi);
-                load_group(V.y, i0, cnt, yi);
-                load_group(x, i0, cnt, xi);
-                load_group(V.p, i0, cnt, pi);
-                load_group(V.t, i0, cnt, ti);
-                load_group(V.r0, i0, cnt, r0i);
+                load_sweep<Op>(V.q, i0, cnt, qi);
+                load_sweep<Op>(V.y, i0, cnt, yi);
+                load_sweep<Op>(x, i0, cnt, xi);
+                load_sweep<Op>(V.p, i0, cnt, pi);
+                load_sweep<Op>(V.t, i0, cnt, ti);
+                load_sweep<Op>(V.r0, i0, cnt, r0i);
                 T xn[kGroup], rn[kGroup], wn[kGroup];
 #pragma unroll
                 for (int u = 0; u < kGroup; ++u) {

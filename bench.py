@@ -120,6 +120,19 @@ def flops_per_launch(n, info):
     return info["spmvs"] * 2.0 * nnz_of(n) + info["iters"] * 2.0 * (13 + 8) * N
 
 
+def batched_flops(sizes, nnz, iters, n_repl):
+    """Algorithmic FP64 flops of one batched launch. Per system: 2 flops per
+    stored entry per SpMV (r_0 = b - A x_0 and w_0 = A r_0, two per iteration,
+    three more per residual replacement, the true residual at the end) plus
+    42 flops per row and iteration (the recurrences and dot products of
+    Algorithm 9, as in flops_per_launch)."""
+    import numpy as np
+    sizes, nnz = np.asarray(sizes, dtype=np.float64), np.asarray(nnz, dtype=np.float64)
+    iters, n_repl = np.asarray(iters, dtype=np.float64), np.asarray(n_repl, dtype=np.float64)
+    spmvs = 3.0 + 2.0 * iters + 3.0 * n_repl
+    return float(np.sum(spmvs * 2.0 * nnz + iters * 2.0 * (13 + 8) * sizes))
+
+
 def bytes_per_iter(n, form="stencil"):
     """Algorithmic HBM bytes per iteration of Algorithm 9: 23 N-vector passes
     (phase A reads w r p s z v r0, writes t p s z; phase B reads z x p r s w t
@@ -551,6 +564,12 @@ def batched_case(nsys, steps, barrier):
         its_single += inf["iters"]
         sv.close()
     frac = float(B.sizes[:m].sum()) / float(B.sizes.sum())
+    nnz_sys = B.rowptr[B.row_offset[1:]].astype(np.int64) - B.rowptr[B.row_offset[:-1]].astype(np.int64)
+    fl = batched_flops(B.sizes, nnz_sys, res["iters"], res["n_replacements"])
+    achieved_tf = fl / sec / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_PEAK_TFLOPS, "kernel": "batched_kernel", "flops_per_launch": fl,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz"}
     return {"workload": f"{B.nsys} random sparse systems, sizes log-uniform 1k-64k (total {B.total_rows} rows, "
                         f"{int(B.rowptr[-1])} nnz), rtol {RTOL:g}, one launch replayed from a CUDA graph",
             "value": sec, "unit": "s", "systems_converged": int(np.sum(res["status"] == native.PBCG_OK)),
@@ -560,7 +579,8 @@ def batched_case(nsys, steps, barrier):
             "single_system_solver_est_s": t_single / frac if frac > 0 else None,
             "single_system_sample": f"first {m} systems (largest) solved one per launch, {frac:.2%} of the rows, "
                                     f"scaled by rows",
-            "speedup_vs_single_system_solver": (t_single / frac) / sec if frac > 0 else None}
+            "speedup_vs_single_system_solver": (t_single / frac) / sec if frac > 0 else None,
+            "roofline": roofline}
 
 
 def adjoint_case(n, barrier):
